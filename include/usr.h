@@ -1,0 +1,217 @@
+/*
+ * usr.h -- C ABI of libusr: u-series electrostatic energy, forces and
+ * potentials for point charges in an orthorhombic periodic box, evaluated on
+ * one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * Method: Predescu et al., "The u-series: a separable decomposition for
+ * electrostatics computation with improved accuracy", arXiv:1911.01377.
+ *   E = E_near + E_far + E_self                          (Eq. 3 with Eqs. 19-22)
+ *   E_near = 1/2 sum_{i != j, images} q_i q_j N(r_ij), N(r) = 1/r - F(r) for
+ *            r < r_c and 0 beyond                          (Eq. 20)
+ *   E_far  = far part, the Gaussians of F(r) summed over all periodic images
+ *            with the k = 0 term dropped (Eqs. 4, 9); evaluated by Gaussian
+ *            charge spreading onto a grid, three per-axis 1D convolutions per
+ *            Gaussian term (Eqs. 31-32, Sec. V) and interpolation back to the
+ *            charges; N terms kept by the bound of Eq. 33
+ *   E_self = -1/2 F(0) sum q_i^2                           (Eq. 10's self term)
+ * Units: charges in e, lengths in Angstrom, Coulomb constant 1 (energies in
+ * e^2/Angstrom, forces in e^2/Angstrom^2, potentials in e/Angstrom).
+ *
+ * Conventions for every entry point:
+ *   - All pointers are owned by the caller; the library never frees them.
+ *   - "device" pointers must be CUDA device (or managed) memory on the
+ *     context's device; "host" pointers ordinary host memory (pinned memory
+ *     makes the copies asynchronous and faster).
+ *   - Position/charge and output arrays are float4-packed (x, y, z, q) and
+ *     (Fx, Fy, Fz, phi) rows, n rows, 16-byte aligned.
+ *   - Positions may lie outside the box; they are wrapped periodically.
+ *   - Work is enqueued on the given CUDA stream (cudaStream_t passed as void*,
+ *     NULL = legacy default stream) and returns before the GPU finishes,
+ *     except where an entry point says it synchronises.  A context must not
+ *     be used from two host threads or on two streams at the same time.
+ *   - No entry point throws, traps or aborts.  Problems found on the GPU
+ *     (non-finite inputs) set a status word read by usr_last_device_status.
+ */
+#ifndef USR_H
+#define USR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    USR_OK = 0,
+    USR_ERR_ARG = 1,        /* null or misaligned pointer, n < 0, unknown enum value */
+    USR_ERR_BOX = 2,        /* geometry the GPU path does not support (see usr_plan) */
+    USR_ERR_NONFINITE = 3,  /* a coordinate was NaN or infinite (found on the GPU) */
+    USR_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    USR_ERR_OOM = 5,        /* device memory allocation failed */
+    USR_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
+    USR_ERR_CAPACITY = 7    /* more atoms than the context was created for */
+} usr_status;
+
+/* Arithmetic of the per-axis far-part convolutions. */
+typedef enum {
+    USR_CONV_FP32 = 0       /* FP32 CUDA-core GEMMs with FP32 accumulation */
+} usr_conv;
+
+/* Presets: the parameter rows printed in Table 2 (b = 2) and Table 1. */
+typedef enum {
+    USR_PRESET_C0_B2 = 0,   /* Table 2 row 1: C0 construction, Eq. 19 */
+    USR_PRESET_C1_B2 = 1,   /* Table 2 row 2: C1 construction, Eq. 24 (recommended, Sec. VI) */
+    USR_PRESET_C2_B2 = 2,   /* Table 2 row 3: C2 construction, Eq. 28 */
+    USR_PRESET_T1_A = 3,    /* Table 1 row 1: C2 point of the C1 family, b = 1.6298 */
+    USR_PRESET_T1_B = 4,    /* Table 1 row 2: b = 1.3207 */
+    USR_PRESET_T1_C = 5     /* Table 1 row 3: b = 1.2181 */
+} usr_preset;
+
+/*
+ * One u-series construction.  The far function at sigma = r_c / r0 (Eq. 23) is
+ *   F(r) = c [ w0 exp(-r^2 / (2 s0^2 sigma^2)) + sum_{j>=1} b^-j exp(-r^2 / (2 b^2j sigma^2)) ],
+ *   c = 2 ln(b) / sqrt(2 pi sigma^2)                               (Eqs. 19, 24, 28)
+ * (Eq. 28's narrow term is taken unnormalised in s0: Table 2's third row
+ * satisfies Eq. 27 only under that reading.)
+ */
+typedef struct {
+    double b;          /* base, b > 1 */
+    double r0;         /* r_c / sigma */
+    double w0;         /* weight of the narrowest Gaussian (1 for C0) */
+    double s0;         /* width factor of the narrowest Gaussian (1 for C0, C1) */
+    int n_terms;       /* Gaussians on the far grid; 0 = smallest N whose Eq. 33 bound <= trunc_eps */
+    double trunc_eps;  /* used when n_terms == 0; 0 means 1e-9 */
+} usr_series;
+
+typedef struct {
+    double box[3];               /* box side lengths L_x, L_y, L_z (Angstrom, > 0) */
+    int grid[3];                 /* far-part grid points per axis */
+    double r_c;                  /* near-part cutoff; sigma = r_c / r0 */
+    usr_series series;
+    double spread_sigma_over_h;  /* spreading Gaussian width / largest grid spacing; 0 = 1.0 */
+    int spread_points;           /* spreading stencil points per axis (even, 8..16); 0 = 12 */
+    usr_conv conv;
+    int max_atoms;               /* capacity of the context (rows per evaluation) */
+} usr_params;
+
+/* Quantities derived from usr_params (all host-side, FP64). */
+typedef struct {
+    double sigma;          /* r_c / r0 */
+    double F0;             /* F(0) of the full series, the self term constant */
+    double spread_sigma;   /* sigma_s of the spreading Gaussian */
+    double h[3];           /* grid spacings L / grid */
+    double trunc_bound;    /* Eq. 33 bound for the chosen n_terms */
+    int n_terms;           /* Gaussians on the far grid */
+    int cells[3];          /* cell-list cells per axis, floor(L / r_c) */
+    int poly_degree;       /* degree of the FP32 polynomial for the wide terms of F */
+    int n_explicit;        /* leading Gaussians of F evaluated explicitly in the pair kernel */
+    double poly_max_err;   /* max |error| of that polynomial on [0, r_c], relative to F(0) */
+} usr_plan_info;
+
+/* Fill *out with a preset row (n_terms = 0, trunc_eps = 0).  Host only. */
+usr_status usr_series_preset(int preset, usr_series* out);
+
+/*
+ * Validate parameters and derive the plan without touching the GPU.
+ * USR_ERR_BOX when: any L, grid or r_c is non-positive; fewer than 3 cells
+ * per axis (r_c > L/3); a grid axis has fewer than spread_points + 8 points;
+ * or the narrowest kept Gaussian is not wider than sqrt(2) sigma_s (Eq. 32's
+ * deconvolved widths sqrt(sigma_j^2 - 2 sigma_s^2) must be real).
+ * USR_ERR_ARG for null pointers or out-of-range series/stencil values.
+ */
+usr_status usr_plan(const usr_params* p, usr_plan_info* out);
+
+typedef struct usr_ctx usr_ctx;
+
+/*
+ * Create a context on the current CUDA device: runs usr_plan, allocates all
+ * device scratch for up to p->max_atoms atoms (owned by the context) and
+ * uploads the tables.  Synchronises the device.  *out is NULL on failure.
+ */
+usr_status usr_init(const usr_params* p, usr_ctx** out);
+
+/* Free a context and its device memory (NULL is ignored).  Synchronises. */
+void usr_destroy(usr_ctx* ctx);
+
+/* Derived quantities of a context. */
+usr_status usr_info(const usr_ctx* ctx, usr_plan_info* out);
+
+/*
+ * One evaluation, enqueued on `stream`, no host synchronisation, no
+ * allocation (usable inside CUDA graph capture).
+ *   xyzq   device, n rows (x, y, z, q) float32, caller order, read only
+ *   out    device, n rows (Fx, Fy, Fz, phi) float32, caller order; F_i = -dE/dr_i,
+ *          phi_i = dE/dq_i (the potential at i with i's self term included)
+ *   energy device, 4 doubles: E, E_near, E_far, E_self (may be NULL)
+ * n = 0 writes zero energies.  USR_ERR_CAPACITY if n > max_atoms.
+ */
+usr_status usr_eval(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
+
+/*
+ * The same evaluation from host memory: copies xyzq (host) to the device,
+ * evaluates, copies out (host) and energy (host, 4 doubles, may be NULL)
+ * back, then synchronises `stream`.
+ */
+usr_status usr_eval_host(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
+
+/*
+ * Synchronise the context's last stream and return the device status of the
+ * evaluations since the previous call (USR_OK or USR_ERR_NONFINITE), then
+ * clear it.
+ */
+usr_status usr_last_device_status(usr_ctx* ctx);
+
+/* Static description of a status code. */
+const char* usr_status_string(usr_status s);
+
+/* ---- inspection entry points used by the parity tests ---------------- */
+
+/*
+ * Bin and sort only (the cell list of the near part).  Device outputs:
+ *   cell       n ints, cell id of each atom (caller order), id = (cz*ny + cy)*nx + cx
+ *   perm       n ints, caller index of the atom at each sorted position
+ *              (sorted by cell, then by caller index)
+ *   cell_start ncell + 1 ints, first sorted position of each cell
+ *   xw         n rows float4 in sorted order: wrapped x, y, z and q
+ * The cell predicate is the single-precision one documented in the oracle.
+ */
+usr_status usr_debug_cells(usr_ctx* ctx, int n, const float* xyzq, int* cell, int* perm,
+                           int* cell_start, float* xw, void* stream);
+
+/*
+ * Pair list of the near part, summarised per atom (caller order): the number
+ * of partners j != i with r^2 < r_c^2 under the single-precision predicate,
+ * and the wrap-around sum of splitmix64(j) over them (j = caller index).
+ */
+usr_status usr_debug_pairs(usr_ctx* ctx, int n, const float* xyzq, int* count, uint64_t* hash,
+                           void* stream);
+
+/* Keep (on != 0) or stop keeping the near and far parts of each usr_eval. */
+usr_status usr_set_keep_parts(usr_ctx* ctx, int on);
+
+/*
+ * Near and far parts of the last usr_eval on this context (which must have
+ * run with usr_set_keep_parts on; USR_ERR_ARG otherwise), caller order, n
+ * rows float4 each (device; either may be NULL):
+ *   near: (F_near, phi_near) of Eq. 20;  far: (F_far, phi_far) of the grid
+ *   part, phi_far without the self term.
+ */
+usr_status usr_debug_parts(usr_ctx* ctx, float* near_out, float* far_out, void* stream);
+
+/* ---- timing ------------------------------------------------------------ */
+
+enum { USR_NSTAGES = 7 };  /* bin, near, spread, conv_x, conv_y, conv_z, gather */
+
+/* Record CUDA events between the stages of every usr_eval (on its stream). */
+usr_status usr_set_profiling(usr_ctx* ctx, int on);
+
+/*
+ * Milliseconds of each stage of the last profiled usr_eval (synchronises).
+ * ms must hold USR_NSTAGES floats.
+ */
+usr_status usr_stage_times(usr_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* USR_H */

@@ -1,0 +1,445 @@
+/*
+ * usr_api.cu -- the C ABI of libusr (declared in include/usr.h): context
+ * creation (plan + device allocation + table upload), the evaluation
+ * sequence on one stream, host-buffer evaluation, status and inspection.
+ *
+ * Evaluation sequence (one stream, no host synchronisation, no allocation):
+ *   bin + sort (cell list) -> near pair kernel (Eq. 20) -> spread ->
+ *   x / y / z convolution passes (Sec. V, Eqs. 31-32) -> gather + combine +
+ *   FP64 energy reduction.
+ */
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "usr_internal.h"
+
+using usr::Plan;
+
+struct usr_ctx {
+    Plan plan;
+    int device = 0;
+    int max_atoms = 0;
+    int ncell = 0;
+    long long G = 0;
+    usr::BoxF boxf;
+    usr::NearArgs near;
+    usr::GridArgs grid;
+    // cell list
+    int *d_count = nullptr, *d_cell_of = nullptr, *d_slot = nullptr, *d_cell_start = nullptr;
+    int *d_unsorted = nullptr, *d_perm = nullptr, *d_status = nullptr;
+    float4 *d_wpos = nullptr, *d_spos = nullptr, *d_near = nullptr;
+    // grids and convolution tables
+    float *d_rho = nullptr, *d_X = nullptr, *d_Y = nullptr, *d_psi = nullptr;
+    float *d_Bx = nullptr, *d_Ay = nullptr, *d_Az = nullptr, *d_wx = nullptr, *d_wy = nullptr, *d_wz = nullptr;
+    double *d_spread_partial = nullptr, *d_mean = nullptr, *d_gather_partial = nullptr, *d_energy = nullptr;
+    unsigned int* d_counters = nullptr;
+    // host-buffer staging and inspection
+    float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
+    bool keep_parts = false;
+    bool parts_valid = false;
+    // profiling
+    bool prof = false;
+    bool prof_valid = false;
+    cudaEvent_t ev[USR_NSTAGES + 1];
+    bool ev_made = false;
+    cudaStream_t last_stream = nullptr;
+    int last_n = 0;
+};
+
+namespace {
+
+template <typename T>
+usr_status dalloc(T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? USR_ERR_OOM : USR_ERR_CUDA;
+    }
+    return USR_OK;
+}
+
+void free_all(usr_ctx* c)
+{
+    void* ptrs[] = {c->d_count, c->d_cell_of, c->d_slot, c->d_cell_start, c->d_unsorted, c->d_perm, c->d_status,
+                    c->d_wpos, c->d_spos, c->d_near, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
+                    c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
+                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->ev_made)
+        for (auto& e : c->ev) cudaEventDestroy(e);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+usr_status check_launch()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? USR_OK : USR_ERR_CUDA;
+}
+
+void fill_box(const Plan& P, usr::BoxF& b)
+{
+    for (int a = 0; a < 3; ++a) {
+        b.L[a] = (float)P.L[a];
+        b.invL[a] = (float)(1.0 / P.L[a]);
+        b.cs[a] = (float)((double)P.cells[a] / P.L[a]);
+        b.gs[a] = (float)((double)P.n[a] / P.L[a]);
+        b.nc[a] = P.cells[a];
+        b.n[a] = P.n[a];
+    }
+}
+
+usr_status upload_tables(usr_ctx* c)
+{
+    const Plan& P = c->plan;
+    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    std::vector<float> Bx((size_t)nx * N * nx), Ay((size_t)N * ny * ny), Az((size_t)nz * N * nz);
+    std::vector<float> wx((size_t)N * nx), wy((size_t)N * ny), wz((size_t)N * nz);
+    for (int j = 0; j < N; ++j) {
+        for (int k = 0; k < nx; ++k)
+            for (int m = 0; m < nx; ++m)
+                Bx[(size_t)k * N * nx + j * nx + m] = (float)P.ktil[0][j][((m - k) % nx + nx) % nx];
+        for (int m = 0; m < ny; ++m)
+            for (int k = 0; k < ny; ++k)
+                Ay[((size_t)j * ny + m) * ny + k] = (float)P.ktil[1][j][((m - k) % ny + ny) % ny];
+        for (int m = 0; m < nz; ++m)
+            for (int k = 0; k < nz; ++k)
+                Az[(size_t)m * N * nz + j * nz + k] = (float)(P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz]);
+        for (int m = 0; m < nx; ++m) wx[(size_t)j * nx + m] = (float)P.mu[0][j];
+        for (int k = 0; k < ny; ++k) wy[(size_t)j * ny + k] = (float)P.mu[1][j];
+        for (int k = 0; k < nz; ++k) wz[(size_t)j * nz + k] = (float)(P.scale[j] * P.mu[2][j]);
+    }
+    struct Up { float* d; const std::vector<float>* h; } ups[] = {
+        {c->d_Bx, &Bx}, {c->d_Ay, &Ay}, {c->d_Az, &Az}, {c->d_wx, &wx}, {c->d_wy, &wy}, {c->d_wz, &wz}};
+    for (auto& u : ups)
+        if (cudaMemcpy(u.d, u.h->data(), sizeof(float) * u.h->size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return USR_ERR_CUDA;
+    return USR_OK;
+}
+
+void fill_args(usr_ctx* c)
+{
+    const Plan& P = c->plan;
+    fill_box(P, c->boxf);
+    usr::NearArgs& a = c->near;
+    std::memset(&a, 0, sizeof(a));
+    a.box = c->boxf;
+    a.rc2 = (float)(P.p.r_c * P.p.r_c);
+    a.two_over_rc2 = (float)(2.0 / (P.p.r_c * P.p.r_c));
+    a.n_explicit = P.n_explicit;
+    for (int e = 0; e < P.n_explicit; ++e) {
+        a.ea[e] = (float)P.ea[e];
+        a.einv[e] = (float)P.einv[e];
+    }
+    for (int d = 0; d <= usr::kMaxPolyDeg; ++d) a.poly[d] = (float)P.poly[d];
+    usr::GridArgs& g = c->grid;
+    std::memset(&g, 0, sizeof(g));
+    g.box = c->boxf;
+    for (int ax = 0; ax < 3; ++ax) {
+        g.hh[ax] = (float)(P.h[ax] * P.h[ax] / (2.0 * P.sigma_s * P.sigma_s));
+        g.dfac[ax] = (float)(P.h[ax] / (P.sigma_s * P.sigma_s));
+    }
+    g.F0 = (float)P.F0;
+}
+
+int spread_blocks(const Plan& P)
+{
+    int nb = 1;
+    for (int a = 0; a < 3; ++a) nb *= (P.n[a] + usr::kBrick - 1) / usr::kBrick;
+    return nb;
+}
+
+usr_status check_device(const usr_ctx* c)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return USR_ERR_CUDA;
+    return dev == c->device ? USR_OK : USR_ERR_ARG;
+}
+
+/* The evaluation sequence; xyzq/out are device pointers already checked. */
+usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* energy, cudaStream_t st)
+{
+    const Plan& P = c->plan;
+    double* en = energy ? energy : c->d_energy;
+    c->last_stream = st;
+    c->last_n = n;
+    c->parts_valid = false;
+    c->prof_valid = false;
+    if (n == 0) {
+        if (cudaMemsetAsync(en, 0, 4 * sizeof(double), st) != cudaSuccess) return USR_ERR_CUDA;
+        return USR_OK;
+    }
+    auto mark = [&](int k) {
+        if (c->prof) cudaEventRecord(c->ev[k], st);
+    };
+    mark(0);
+    usr::launch_bin(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos, c->d_cell_start,
+                    c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    mark(1);
+    const int block = (n <= 48 * c->ncell) ? 64 : 128;
+    usr::launch_near(c->ncell, block, P.poly_deg, c->d_spos, c->d_cell_start, c->near, c->d_near, st);
+    mark(2);
+    usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_rho, c->d_spread_partial, c->d_counters,
+                       c->d_mean, st);
+    mark(3);
+    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const long long G = c->G;
+    {   // x pass: all terms
+        usr::ConvGemm g{};
+        g.M = ny * nz; g.N = N * nx; g.K = nx;
+        g.A = c->d_rho; g.lda = nx;
+        g.B = c->d_Bx; g.ldb = (long long)N * nx;
+        g.C = c->d_X; g.ldc = nx;
+        g.nb2 = 1; g.nsplit = nx; g.c_split = G;
+        g.mode = 1; g.dcw = c->d_wx; g.mean = c->d_mean;
+        usr::launch_conv(g, 1, st);
+    }
+    mark(4);
+    {   // y pass: batched over (term, z)
+        usr::ConvGemm g{};
+        g.M = ny; g.N = nx; g.K = ny;
+        g.A = c->d_Ay; g.lda = ny; g.a_s1 = (long long)ny * ny; g.a_s2 = 0;
+        g.B = c->d_X; g.ldb = nx; g.b_s1 = G; g.b_s2 = (long long)ny * nx;
+        g.C = c->d_Y; g.ldc = nx; g.c_s1 = G; g.c_s2 = (long long)ny * nx;
+        g.nb2 = nz; g.nsplit = 1 << 30; g.c_split = 0;
+        g.mode = 2; g.dcw = c->d_wy; g.dcw_s1 = ny;
+        usr::launch_conv(g, N * nz, st);
+    }
+    mark(5);
+    {   // z pass: sum over terms folded into K
+        usr::ConvGemm g{};
+        g.M = nz; g.N = nx * ny; g.K = N * nz;
+        g.A = c->d_Az; g.lda = (long long)N * nz;
+        g.B = c->d_Y; g.ldb = (long long)nx * ny;
+        g.C = c->d_psi; g.ldc = (long long)nx * ny;
+        g.nb2 = 1; g.nsplit = 1 << 30; g.c_split = 0;
+        g.mode = 2; g.dcw = c->d_wz; g.dcw_s1 = 0;
+        usr::launch_conv(g, 1, st);
+    }
+    mark(6);
+    usr::launch_gather(P.P, n, c->d_spos, c->d_perm, c->d_near, c->d_psi, c->grid, out,
+                       c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
+                       c->d_gather_partial, c->d_counters + 1, en, st);
+    mark(7);
+    usr_status s = check_launch();
+    if (s == USR_OK) {
+        c->parts_valid = c->keep_parts;
+        c->prof_valid = c->prof;
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
+{
+    if (!out) return USR_ERR_ARG;
+    *out = nullptr;
+    if (!p) return USR_ERR_ARG;
+    usr_ctx* c = new (std::nothrow) usr_ctx();
+    if (!c) return USR_ERR_OOM;
+    usr_status s = usr::make_plan(p, &c->plan);
+    if (s != USR_OK) {
+        delete c;
+        return s;
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return USR_ERR_CUDA;
+    }
+    const Plan& P = c->plan;
+    c->max_atoms = p->max_atoms;
+    c->ncell = P.cells[0] * P.cells[1] * P.cells[2];
+    c->G = (long long)P.n[0] * P.n[1] * P.n[2];
+    const size_t na = (size_t)(c->max_atoms > 0 ? c->max_atoms : 1);
+    const size_t N = (size_t)P.N;
+    const int nsb = spread_blocks(P);
+    const int ngb = usr::gather_blocks(c->max_atoms > 0 ? c->max_atoms : 1);
+    fill_args(c);
+#define ALLOC(ptr, cnt) \
+    if ((s = dalloc(&(ptr), (cnt))) != USR_OK) { free_all(c); delete c; return s; }
+    ALLOC(c->d_count, (size_t)c->ncell);
+    ALLOC(c->d_cell_start, (size_t)c->ncell + 1);
+    ALLOC(c->d_cell_of, na);
+    ALLOC(c->d_slot, na);
+    ALLOC(c->d_unsorted, na);
+    ALLOC(c->d_perm, na);
+    ALLOC(c->d_status, 1);
+    ALLOC(c->d_wpos, na);
+    ALLOC(c->d_spos, na);
+    ALLOC(c->d_near, na);
+    ALLOC(c->d_rho, (size_t)c->G);
+    ALLOC(c->d_X, N * (size_t)c->G);
+    ALLOC(c->d_Y, N * (size_t)c->G);
+    ALLOC(c->d_psi, (size_t)c->G);
+    ALLOC(c->d_Bx, (size_t)P.n[0] * N * P.n[0]);
+    ALLOC(c->d_Ay, N * P.n[1] * P.n[1]);
+    ALLOC(c->d_Az, (size_t)P.n[2] * N * P.n[2]);
+    ALLOC(c->d_wx, N * P.n[0]);
+    ALLOC(c->d_wy, N * P.n[1]);
+    ALLOC(c->d_wz, N * P.n[2]);
+    ALLOC(c->d_spread_partial, (size_t)nsb);
+    ALLOC(c->d_mean, 1);
+    ALLOC(c->d_gather_partial, (size_t)ngb * 4);
+    ALLOC(c->d_energy, 4);
+    ALLOC(c->d_counters, 2);
+    ALLOC(c->d_in, na);
+    ALLOC(c->d_out, na);
+    ALLOC(c->d_near_dbg, na);
+    ALLOC(c->d_far_dbg, na);
+#undef ALLOC
+    if (cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return USR_ERR_CUDA;
+    }
+    if ((s = upload_tables(c)) != USR_OK) {
+        free_all(c);
+        delete c;
+        return s;
+    }
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    c->ev_made = true;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return USR_ERR_CUDA;
+    }
+    *out = c;
+    return USR_OK;
+}
+
+extern "C" void usr_destroy(usr_ctx* c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+extern "C" usr_status usr_info(const usr_ctx* c, usr_plan_info* out)
+{
+    if (!c || !out) return USR_ERR_ARG;
+    *out = c->plan.info;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_eval(usr_ctx* c, int n, const float* xyzq, float* out, double* energy, void* stream)
+{
+    if (!c || n < 0) return USR_ERR_ARG;
+    if (n > c->max_atoms) return USR_ERR_CAPACITY;
+    if (n > 0 && (!xyzq || !out || !aligned16(xyzq) || !aligned16(out))) return USR_ERR_ARG;
+    if (energy && ((uintptr_t)energy & 7u)) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    return run_eval(c, n, (const float4*)xyzq, (float4*)out, energy, (cudaStream_t)stream);
+}
+
+extern "C" usr_status usr_eval_host(usr_ctx* c, int n, const float* xyzq, float* out, double* energy, void* stream)
+{
+    if (!c || n < 0) return USR_ERR_ARG;
+    if (n > c->max_atoms) return USR_ERR_CAPACITY;
+    if (n > 0 && (!xyzq || !out)) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0 && cudaMemcpyAsync(c->d_in, xyzq, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    s = run_eval(c, n, c->d_in, c->d_out, c->d_energy, st);
+    if (s != USR_OK) return s;
+    if (n > 0 && cudaMemcpyAsync(out, c->d_out, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    if (energy && cudaMemcpyAsync(energy, c->d_energy, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? USR_OK : USR_ERR_CUDA;
+}
+
+extern "C" usr_status usr_last_device_status(usr_ctx* c)
+{
+    if (!c) return USR_ERR_ARG;
+    if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return USR_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return USR_ERR_CUDA;
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return USR_ERR_CUDA;
+    return (v & 1) ? USR_ERR_NONFINITE : USR_OK;
+}
+
+extern "C" usr_status usr_debug_cells(usr_ctx* c, int n, const float* xyzq, int* cell, int* perm, int* cell_start,
+                                      float* xw, void* stream)
+{
+    if (!c || n < 0 || n > c->max_atoms) return USR_ERR_ARG;
+    if (n > 0 && (!xyzq || !aligned16(xyzq) || !cell || !perm || !cell_start || !xw || !aligned16(xw)))
+        return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    if (n == 0) return USR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    usr::launch_bin(n, (const float4*)xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
+                    c->d_cell_start, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    cudaMemcpyAsync(cell, c->d_cell_of, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(perm, c->d_perm, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(cell_start, c->d_cell_start, sizeof(int) * ((size_t)c->ncell + 1), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(xw, c->d_spos, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    return check_launch();
+}
+
+extern "C" usr_status usr_debug_pairs(usr_ctx* c, int n, const float* xyzq, int* count, uint64_t* hash, void* stream)
+{
+    if (!c || n < 0 || n > c->max_atoms) return USR_ERR_ARG;
+    if (n > 0 && (!xyzq || !aligned16(xyzq) || !count || !hash)) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    if (n == 0) return USR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    usr::launch_bin(n, (const float4*)xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
+                    c->d_cell_start, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    usr::launch_pairs(c->ncell, c->d_spos, c->d_cell_start, c->d_perm, c->near, count,
+                      (unsigned long long*)hash, st);
+    return check_launch();
+}
+
+extern "C" usr_status usr_set_keep_parts(usr_ctx* c, int on)
+{
+    if (!c) return USR_ERR_ARG;
+    c->keep_parts = on != 0;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_debug_parts(usr_ctx* c, float* near_out, float* far_out, void* stream)
+{
+    if (!c) return USR_ERR_ARG;
+    if (!c->parts_valid) return USR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(float4) * (size_t)c->last_n;
+    if (near_out) cudaMemcpyAsync(near_out, c->d_near_dbg, bytes, cudaMemcpyDeviceToDevice, st);
+    if (far_out) cudaMemcpyAsync(far_out, c->d_far_dbg, bytes, cudaMemcpyDeviceToDevice, st);
+    return check_launch();
+}
+
+extern "C" usr_status usr_set_profiling(usr_ctx* c, int on)
+{
+    if (!c) return USR_ERR_ARG;
+    c->prof = on != 0;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
+{
+    if (!c || !ms) return USR_ERR_ARG;
+    if (!c->prof_valid) return USR_ERR_ARG;
+    if (cudaEventSynchronize(c->ev[USR_NSTAGES]) != cudaSuccess) return USR_ERR_CUDA;
+    for (int k = 0; k < USR_NSTAGES; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]) != cudaSuccess) return USR_ERR_CUDA;
+        ms[k] = t;
+    }
+    return USR_OK;
+}

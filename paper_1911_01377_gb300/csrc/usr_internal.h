@@ -1,0 +1,106 @@
+/*
+ * usr_internal.h -- internal declarations shared by the libusr translation
+ * units: the host-side plan (FP64 set-up of the u-series tables) and the
+ * argument structs and launchers of the device kernels.
+ */
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/usr.h"
+
+namespace usr {
+
+constexpr int kMaxPolyDeg = 24;
+constexpr int kMaxExplicit = 8;
+constexpr int kMaxTerms = 16;
+constexpr int kBrick = 8;           // spreading/interpolation brick edge (grid points)
+
+/* Host plan: everything usr_init derives from usr_params, in FP64. */
+struct Plan {
+    usr_params p;
+    usr_plan_info info;
+    double L[3];
+    int n[3];
+    double h[3];
+    double sigma, c, F0;
+    double sigma_s;
+    int P;                               // stencil points per axis
+    int N;                               // far-grid Gaussians
+    std::vector<double> a, s;            // full real-space term table (a_j, s_j)
+    // pair kernel: F(u = r^2) = sum_{e < n_explicit} ea_e exp(-u * einv_e) + poly(2u/r_c^2 - 1)
+    int n_explicit;
+    std::vector<char> expl;              // expl[j]: term j is one of the explicit Gaussians
+    double ea[kMaxExplicit], einv[kMaxExplicit];
+    int poly_deg;
+    double poly[kMaxPolyDeg + 1];
+    // far grid: per term j < N, axis a: zero-mean periodised 1D kernel ktil[a][j][d] (d = 0..n-1)
+    // and its mean mu[a][j]; scale[j] multiplies the term (applied in the z pass)
+    std::vector<double> ktil[3][kMaxTerms];
+    double mu[3][kMaxTerms];
+    double scale[kMaxTerms];
+    int cells[3];
+};
+
+/* Build the plan (host only).  Returns USR_OK or an error. */
+usr_status make_plan(const usr_params* p, Plan* out);
+
+/* Canonical single-precision box constants per axis (see the oracle's predicate). */
+struct BoxF {
+    float L[3];       // (float)L
+    float invL[3];    // (float)(1/L)
+    float cs[3];      // (float)(nc / L)
+    float gs[3];      // (float)(n / L): grid coordinate scale
+    int nc[3];
+    int n[3];
+};
+
+struct NearArgs {
+    BoxF box;
+    float rc2;            // (float)(r_c^2)
+    float two_over_rc2;   // 2 / r_c^2
+    int n_explicit;
+    float ea[kMaxExplicit];
+    float einv[kMaxExplicit];
+    float poly[kMaxPolyDeg + 1];
+};
+
+struct GridArgs {
+    BoxF box;
+    float hh[3];          // h^2 / (2 sigma_s^2): exponent factor per stencil step
+    float dfac[3];        // h / sigma_s^2: derivative factor
+    float F0;             // self-interaction constant
+};
+
+struct ConvGemm {
+    int M, N, K;
+    const float* A; long long lda, a_s1, a_s2;   // A[b1][b2][m][k] = A + b1*a_s1 + b2*a_s2 + m*lda + k
+    const float* B; long long ldb, b_s1, b_s2;   // B[b1][b2][k][n]
+    float* C; long long ldc, c_s1, c_s2;         // C[b1][b2][m][n]
+    int nb2;                                     // batch = b1 * nb2 + b2
+    int nsplit; long long c_split;               // column block j = n / nsplit goes to C + j*c_split
+    int mode;                                    // 0 none, 1 rowsum(A) * colw[n], 2 sum_k roww[k] B[k][n]
+    const float* dcw; long long dcw_s1;          // weights; per-b1 offset dcw_s1
+    const double* mean;                          // mode 1: subtract K*mean from the row sums (may be null)
+};
+
+// ---- launchers (all enqueue on `st`) ----
+void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                float4* wpos, int* cell_start, int* unsorted, int* perm, float4* spos, int* status,
+                cudaStream_t st);
+void launch_near(int ncell, int block, int deg, const float4* spos, const int* cell_start,
+                 const NearArgs& a, float4* out, cudaStream_t st);
+void launch_pairs(int ncell, const float4* spos, const int* cell_start, const int* perm, const NearArgs& a,
+                  int* count, unsigned long long* hash, cudaStream_t st);
+void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* rho,
+                   double* partial, unsigned int* counter, double* mean, cudaStream_t st);
+void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
+void launch_gather(int P, int n, const float4* spos, const int* perm, const float4* near_out, const float* psi,
+                   const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg, double* partial,
+                   unsigned int* counter, double* energy, cudaStream_t st);
+int gather_blocks(int n);
+
+}  // namespace usr

@@ -1,0 +1,306 @@
+/*
+ * usr_setup.cpp -- host-side FP64 set-up of the u-series tables (runs once
+ * per context, no GPU work):
+ *   - the term table of the far function (Eqs. 19, 24, 28 at sigma = r_c / r0, Eq. 23)
+ *   - the self constant F(0) = c (w0 + 1 / (b - 1))            (Eq. 10's self term)
+ *   - the number N of far Gaussians from the bound of Eq. 33
+ *   - the pair-kernel form of F: explicit Gaussians for the narrow terms and a
+ *     Chebyshev-fitted polynomial in r^2 for the rest
+ *   - the periodised 1D kernels of the per-axis convolutions: Eq. 32's
+ *     k-space kernel divided by the spreading transform |S(k)|^2 makes each
+ *     term a Gaussian of width sqrt(s_j^2 - 2 sigma_s^2), separable per axis
+ *     (Eq. 31), periodised on the grid and split into its mean and a
+ *     zero-mean part (the split keeps the wide terms accurate in FP32).
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "usr_internal.h"
+
+namespace usr {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct PresetRow {
+    double b, r0, w0, s0;
+};
+
+/* Table 2 (rows C0, C1, C2 at b = 2) and Table 1 (C2 points of the C1 family). */
+const PresetRow kPresets[6] = {
+    {2.0, 1.84309078551204634, 1.00000000000000000, 1.00000000000000000},
+    {2.0, 1.98925368390802627, 0.994446492762232252, 1.00000000000000000},
+    {2.0, 2.39427106444012661, 0.892857784448501290, 1.02474173246377476},
+    {1.62976708826776469, 2.75200266680234223, 1.00780697934380681, 1.0},
+    {1.32070036405934420, 4.39145547116383425, 1.00188914114811980, 1.0},
+    {1.21812525709410644, 5.63552881512711037, 1.00090146156033341, 1.0},
+};
+
+/* Eq. 33: relative truncation bound of the far energy with N terms. */
+double trunc_bound(int N, double b, double sigma, double Lmax)
+{
+    double e = 2.0 * N * std::log(b) - 2.0 * (std::pow(b, 2.0 * N) - 1.0) * kPi * kPi * sigma * sigma / (Lmax * Lmax);
+    return std::exp(e);
+}
+
+/* Sum of the non-explicit Gaussians and its u-derivative at u = r^2. */
+void wide_terms(const Plan& P, double u, double* f, double* df)
+{
+    double v = 0.0, d = 0.0;
+    for (int j = (int)P.a.size() - 1; j >= 0; --j) {
+        if (P.expl[j]) continue;
+        double inv = 1.0 / (2.0 * P.s[j] * P.s[j]);
+        double g = P.a[j] * std::exp(-u * inv);
+        v += g;
+        d -= g * inv;
+    }
+    *f = v;
+    *df = d;
+}
+
+/*
+ * Chebyshev interpolation of the wide-term sum on u in [0, r_c^2], written as
+ * monomials in s = 2u / r_c^2 - 1.  Returns the max relative error of the
+ * value (to f(0)) and of the derivative (to max |df/du|) on a dense sample.
+ */
+void fit_poly(const Plan& P, int D, double* mono, double* err_v, double* err_d)
+{
+    double rc2 = P.p.r_c * P.p.r_c;
+    std::vector<double> fs(D + 1), ck(D + 1, 0.0);
+    for (int i = 0; i <= D; ++i) {
+        double s = std::cos(kPi * (i + 0.5) / (D + 1));
+        double df;
+        wide_terms(P, 0.5 * (s + 1.0) * rc2, &fs[i], &df);
+    }
+    for (int k = 0; k <= D; ++k) {
+        double sum = 0.0;
+        for (int i = 0; i <= D; ++i) sum += fs[i] * std::cos(kPi * k * (i + 0.5) / (D + 1));
+        ck[k] = 2.0 * sum / (D + 1);
+    }
+    ck[0] *= 0.5;
+    // monomial coefficients: T_{k+1} = 2 s T_k - T_{k-1}
+    std::vector<double> tkm1(D + 2, 0.0), tk(D + 2, 0.0), tkp1(D + 2, 0.0);
+    for (int i = 0; i <= D; ++i) mono[i] = 0.0;
+    tkm1[0] = 1.0;                  // T_0
+    tk[1] = 1.0;                    // T_1
+    mono[0] += ck[0];
+    if (D >= 1) mono[1] += ck[1];
+    for (int k = 1; k < D; ++k) {
+        std::fill(tkp1.begin(), tkp1.end(), 0.0);
+        for (int i = 0; i <= D; ++i) {
+            if (i + 1 <= D + 1) tkp1[i + 1] += 2.0 * tk[i];
+            tkp1[i] -= tkm1[i];
+        }
+        for (int i = 0; i <= D; ++i) mono[i] += ck[k + 1] * tkp1[i];
+        tkm1 = tk;
+        tk = tkp1;
+    }
+    double f0, d0;
+    wide_terms(P, 0.0, &f0, &d0);
+    double emax_v = 0.0, emax_d = 0.0, dmax = 0.0;
+    for (int t = 0; t <= 4000; ++t) {
+        double s = -1.0 + 2.0 * t / 4000.0;
+        double pv = 0.0, pd = 0.0;
+        for (int i = D; i >= 0; --i) {
+            pd = pd * s + pv;
+            pv = pv * s + mono[i];
+        }
+        double f, df;
+        wide_terms(P, 0.5 * (s + 1.0) * rc2, &f, &df);
+        pd *= 2.0 / rc2;
+        emax_v = std::max(emax_v, std::fabs(pv - f));
+        emax_d = std::max(emax_d, std::fabs(pd - df));
+        dmax = std::max(dmax, std::fabs(df));
+    }
+    *err_v = emax_v / std::fabs(f0);
+    *err_d = dmax > 0 ? emax_d / dmax : 0.0;
+}
+
+/*
+ * Periodised 1D Gaussian exp(-x^2 / (2 w^2)) on n points of spacing h over a
+ * period L = n h, split into its mean (returned) and zero-mean part (kt).
+ * Narrow kernels use the real-space image sum, wide ones the Poisson
+ * (cosine) series, whose m = 0 term is the mean.
+ */
+double periodic_kernel(double w, double h, int n, std::vector<double>& kt)
+{
+    double L = n * h;
+    kt.assign(n, 0.0);
+    if (w < 0.25 * L) {
+        std::vector<double> k(n, 0.0);
+        int pmax = (int)std::ceil(40.0 * w / L) + 1;
+        for (int d = 0; d < n; ++d) {
+            double x = d * h, v = 0.0;
+            for (int p = -pmax; p <= pmax; ++p) {
+                double y = x + p * L;
+                double e = y * y / (2.0 * w * w);
+                if (e < 745.0) v += std::exp(-e);
+            }
+            k[d] = v;
+        }
+        double mean = 0.0;
+        for (int d = 0; d < n; ++d) mean += k[d];
+        mean /= n;
+        for (int d = 0; d < n; ++d) kt[d] = k[d] - mean;
+        return mean;
+    }
+    double pref = std::sqrt(2.0 * kPi) * w / L;
+    double mean = 1.0;
+    for (int m = 1;; ++m) {
+        double e = 2.0 * kPi * kPi * w * w * (double)m * m / (L * L);
+        if (e > 745.0) break;
+        double g = std::exp(-e);
+        if (m % n == 0) {
+            mean += 2.0 * g;
+            continue;
+        }
+        for (int d = 0; d < n; ++d) kt[d] += 2.0 * g * std::cos(2.0 * kPi * (double)m * d / n);
+    }
+    for (int d = 0; d < n; ++d) kt[d] *= pref;
+    return pref * mean;
+}
+
+}  // namespace
+
+usr_status make_plan(const usr_params* pp, Plan* out)
+{
+    if (!pp || !out) return USR_ERR_ARG;
+    Plan& P = *out;
+    P = Plan();
+    P.p = *pp;
+    const usr_params& p = P.p;
+    const usr_series& se = p.series;
+    if (!(se.b > 1.0) || !(se.r0 > 0.0) || !(se.w0 > 0.0) || !(se.s0 > 0.0) || se.n_terms < 0 ||
+        se.n_terms > kMaxTerms || se.trunc_eps < 0.0 || !std::isfinite(se.b) || !std::isfinite(se.r0))
+        return USR_ERR_ARG;
+    if (p.conv != USR_CONV_FP32) return USR_ERR_ARG;
+    if (p.max_atoms < 0) return USR_ERR_ARG;
+    int Pst = p.spread_points ? p.spread_points : 12;
+    if (Pst < 8 || Pst > 16 || (Pst & 1)) return USR_ERR_ARG;
+    double ratio = p.spread_sigma_over_h > 0.0 ? p.spread_sigma_over_h : 1.0;
+    if (!(p.r_c > 0.0) || !std::isfinite(p.r_c)) return USR_ERR_BOX;
+    for (int a = 0; a < 3; ++a) {
+        if (!(p.box[a] > 0.0) || !std::isfinite(p.box[a]) || p.grid[a] <= 0) return USR_ERR_BOX;
+        P.L[a] = p.box[a];
+        P.n[a] = p.grid[a];
+        P.h[a] = p.box[a] / p.grid[a];
+        if (p.grid[a] < Pst + kBrick) return USR_ERR_BOX;
+        int nc = (int)std::floor(p.box[a] / p.r_c);
+        if (nc < 3) return USR_ERR_BOX;
+        P.cells[a] = std::min(nc, 512);
+    }
+    P.P = Pst;
+    P.sigma = p.r_c / se.r0;
+    P.c = 2.0 * std::log(se.b) / std::sqrt(2.0 * kPi * P.sigma * P.sigma);
+    P.F0 = P.c * (se.w0 + 1.0 / (se.b - 1.0));
+    // full real-space term table
+    P.a.push_back(P.c * se.w0);
+    P.s.push_back(se.s0 * P.sigma);
+    for (int j = 1;; ++j) {
+        double bj = std::pow(se.b, (double)j);
+        if (1.0 / bj < 1e-20) break;
+        P.a.push_back(P.c / bj);
+        P.s.push_back(P.sigma * bj);
+    }
+    double Lmax = std::max(P.L[0], std::max(P.L[1], P.L[2]));
+    // number of far Gaussians, Eq. 33
+    if (se.n_terms > 0) {
+        P.N = se.n_terms;
+    } else {
+        double eps = se.trunc_eps > 0.0 ? se.trunc_eps : 1e-9;
+        P.N = 0;
+        for (int N = 1; N <= kMaxTerms; ++N)
+            if (trunc_bound(N, se.b, P.sigma, Lmax) <= eps) { P.N = N; break; }
+        if (P.N == 0) return USR_ERR_BOX;
+    }
+    // spreading Gaussian and per-term deconvolved widths
+    double hmax = std::max(P.h[0], std::max(P.h[1], P.h[2]));
+    P.sigma_s = ratio * hmax;
+    double dV = P.h[0] * P.h[1] * P.h[2];
+    double norm_s = std::pow(2.0 * kPi * P.sigma_s * P.sigma_s, -3.0);   // two spreading Gaussians
+    for (int j = 0; j < P.N; ++j) {
+        double wc2 = P.s[j] * P.s[j] - 2.0 * P.sigma_s * P.sigma_s;
+        if (!(wc2 > 0.0)) return USR_ERR_BOX;
+        double wc = std::sqrt(wc2);
+        double Aj = P.a[j] * std::pow(P.s[j] / wc, 3.0);
+        P.scale[j] = Aj * dV * dV * norm_s;
+        for (int a = 0; a < 3; ++a) P.mu[a][j] = periodic_kernel(wc, P.h[a], P.n[a], P.ktil[a][j]);
+    }
+    // pair kernel form of F: explicit narrow Gaussians + polynomial in u = r^2
+    double rc2 = p.r_c * p.r_c;
+    P.n_explicit = 0;
+    P.expl.assign(P.a.size(), 0);
+    for (size_t j = 0; j < P.a.size() && P.n_explicit < kMaxExplicit; ++j) {
+        double range = rc2 / (2.0 * P.s[j] * P.s[j]);
+        if (range > 2.5) {
+            P.expl[j] = 1;
+            P.ea[P.n_explicit] = P.a[j];
+            P.einv[P.n_explicit] = 1.0 / (2.0 * P.s[j] * P.s[j]);
+            ++P.n_explicit;
+        }
+    }
+    static const int kDegs[] = {8, 12, 16, 20, 24};
+    P.poly_deg = 0;
+    double ev = 1.0, ed = 1.0;
+    for (int D : kDegs) {
+        fit_poly(P, D, P.poly, &ev, &ed);
+        P.poly_deg = D;
+        if (ev < 2e-9 && ed < 2e-8) break;
+    }
+    for (int i = P.poly_deg + 1; i <= kMaxPolyDeg; ++i) P.poly[i] = 0.0;
+
+    usr_plan_info& I = P.info;
+    std::memset(&I, 0, sizeof(I));
+    I.sigma = P.sigma;
+    I.F0 = P.F0;
+    I.spread_sigma = P.sigma_s;
+    for (int a = 0; a < 3; ++a) { I.h[a] = P.h[a]; I.cells[a] = P.cells[a]; }
+    I.trunc_bound = trunc_bound(P.N, se.b, P.sigma, Lmax);
+    I.n_terms = P.N;
+    I.poly_degree = P.poly_deg;
+    I.n_explicit = P.n_explicit;
+    I.poly_max_err = ev;
+    return USR_OK;
+}
+
+}  // namespace usr
+
+extern "C" usr_status usr_series_preset(int preset, usr_series* out)
+{
+    if (!out || preset < 0 || preset > 5) return USR_ERR_ARG;
+    const usr::PresetRow& r = usr::kPresets[preset];
+    out->b = r.b;
+    out->r0 = r.r0;
+    out->w0 = r.w0;
+    out->s0 = r.s0;
+    out->n_terms = 0;
+    out->trunc_eps = 0.0;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_plan(const usr_params* p, usr_plan_info* out)
+{
+    if (!p || !out) return USR_ERR_ARG;
+    usr::Plan* P = new usr::Plan();
+    usr_status st = usr::make_plan(p, P);
+    if (st == USR_OK) *out = P->info;
+    delete P;
+    return st;
+}
+
+extern "C" const char* usr_status_string(usr_status s)
+{
+    switch (s) {
+        case USR_OK: return "ok";
+        case USR_ERR_ARG: return "invalid argument";
+        case USR_ERR_BOX: return "unsupported geometry or parameters";
+        case USR_ERR_NONFINITE: return "non-finite coordinate";
+        case USR_ERR_CUDA: return "CUDA runtime error";
+        case USR_ERR_OOM: return "device out of memory";
+        case USR_ERR_TIMEOUT: return "device wait timed out";
+        case USR_ERR_CAPACITY: return "more atoms than the context capacity";
+    }
+    return "unknown status";
+}

@@ -1,0 +1,261 @@
+"""Python binding of libusr (include/usr.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls; tensors are
+passed as raw device pointers on the current PyTorch CUDA stream.  There is no
+fallback: if libusr.so is missing or fails to load, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libusr.so")
+
+_c_d = ctypes.c_double
+_c_i = ctypes.c_int
+_c_p = ctypes.c_void_p
+
+USR_OK = 0
+USR_NSTAGES = 7
+STAGES = ("bin", "near", "spread", "conv_x", "conv_y", "conv_z", "gather")
+PRESETS = {"C0_B2": 0, "C1_B2": 1, "C2_B2": 2, "T1_A": 3, "T1_B": 4, "T1_C": 5}
+
+
+class usr_series(ctypes.Structure):
+    _fields_ = [("b", _c_d), ("r0", _c_d), ("w0", _c_d), ("s0", _c_d), ("n_terms", _c_i), ("trunc_eps", _c_d)]
+
+
+class usr_params(ctypes.Structure):
+    _fields_ = [("box", _c_d * 3), ("grid", _c_i * 3), ("r_c", _c_d), ("series", usr_series),
+                ("spread_sigma_over_h", _c_d), ("spread_points", _c_i), ("conv", _c_i), ("max_atoms", _c_i)]
+
+
+class usr_plan_info(ctypes.Structure):
+    _fields_ = [("sigma", _c_d), ("F0", _c_d), ("spread_sigma", _c_d), ("h", _c_d * 3), ("trunc_bound", _c_d),
+                ("n_terms", _c_i), ("cells", _c_i * 3), ("poly_degree", _c_i), ("n_explicit", _c_i),
+                ("poly_max_err", _c_d)]
+
+
+class UsrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {usr_status_string(code)} (status {code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libusr.so (built in-tree by paper_1911_01377_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libusr.so not found at {LIB_PATH}: run paper_1911_01377_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.usr_series_preset.argtypes = [_c_i, ctypes.POINTER(usr_series)]
+        L.usr_plan.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(usr_plan_info)]
+        L.usr_init.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(_c_p)]
+        L.usr_destroy.argtypes = [_c_p]
+        L.usr_destroy.restype = None
+        L.usr_info.argtypes = [_c_p, ctypes.POINTER(usr_plan_info)]
+        L.usr_eval.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
+        L.usr_eval_host.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
+        L.usr_last_device_status.argtypes = [_c_p]
+        L.usr_status_string.argtypes = [_c_i]
+        L.usr_status_string.restype = ctypes.c_char_p
+        L.usr_debug_cells.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]
+        L.usr_debug_pairs.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
+        L.usr_set_keep_parts.argtypes = [_c_p, _c_i]
+        L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
+        L.usr_set_profiling.argtypes = [_c_p, _c_i]
+        L.usr_stage_times.argtypes = [_c_p, ctypes.POINTER(ctypes.c_float)]
+        for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_info", "usr_eval", "usr_eval_host",
+                     "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_set_keep_parts",
+                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times"):
+            getattr(L, name).restype = _c_i
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != USR_OK:
+        raise UsrError(code, where)
+
+
+def usr_status_string(code: int) -> str:
+    return lib().usr_status_string(code).decode()
+
+
+def usr_series_preset(preset) -> usr_series:
+    if isinstance(preset, str):
+        preset = PRESETS[preset]
+    s = usr_series()
+    _check(lib().usr_series_preset(int(preset), ctypes.byref(s)), "usr_series_preset")
+    return s
+
+
+def make_params(box, grid, r_c, series, spread_sigma_over_h=0.0, spread_points=0, conv=0, max_atoms=0,
+                n_terms=0, trunc_eps=0.0) -> usr_params:
+    if isinstance(series, (str, int)):
+        series = usr_series_preset(series)
+    elif not isinstance(series, usr_series):
+        b, r0, w0, s0 = tuple(series)[:4]
+        series = usr_series(b, r0, w0, s0, 0, 0.0)
+    series = usr_series(series.b, series.r0, series.w0, series.s0, int(n_terms or series.n_terms),
+                        float(trunc_eps or series.trunc_eps))
+    p = usr_params()
+    p.box = (_c_d * 3)(*[float(v) for v in box])
+    p.grid = (_c_i * 3)(*[int(v) for v in grid])
+    p.r_c = float(r_c)
+    p.series = series
+    p.spread_sigma_over_h = float(spread_sigma_over_h)
+    p.spread_points = int(spread_points)
+    p.conv = int(conv)
+    p.max_atoms = int(max_atoms)
+    return p
+
+
+def usr_plan(params: usr_params) -> usr_plan_info:
+    info = usr_plan_info()
+    _check(lib().usr_plan(ctypes.byref(params), ctypes.byref(info)), "usr_plan")
+    return info
+
+
+def usr_init(params: usr_params) -> int:
+    h = _c_p()
+    _check(lib().usr_init(ctypes.byref(params), ctypes.byref(h)), "usr_init")
+    return h.value
+
+
+def usr_destroy(ctx: int):
+    lib().usr_destroy(ctx)
+
+
+def usr_info(ctx: int) -> usr_plan_info:
+    info = usr_plan_info()
+    _check(lib().usr_info(ctx, ctypes.byref(info)), "usr_info")
+    return info
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def usr_eval(ctx: int, n: int, xyzq_ptr: int, out_ptr: int, energy_ptr: Optional[int], stream=None):
+    _check(lib().usr_eval(ctx, int(n), xyzq_ptr, out_ptr, energy_ptr, _stream_ptr(stream)), "usr_eval")
+
+
+def usr_eval_host(ctx: int, n: int, xyzq_ptr: int, out_ptr: int, energy_ptr: Optional[int], stream=None):
+    _check(lib().usr_eval_host(ctx, int(n), xyzq_ptr, out_ptr, energy_ptr, _stream_ptr(stream)), "usr_eval_host")
+
+
+def usr_last_device_status(ctx: int) -> int:
+    return lib().usr_last_device_status(ctx)
+
+
+def usr_debug_cells(ctx, n, xyzq_ptr, cell_ptr, perm_ptr, start_ptr, xw_ptr, stream=None):
+    _check(lib().usr_debug_cells(ctx, int(n), xyzq_ptr, cell_ptr, perm_ptr, start_ptr, xw_ptr,
+                                 _stream_ptr(stream)), "usr_debug_cells")
+
+
+def usr_debug_pairs(ctx, n, xyzq_ptr, count_ptr, hash_ptr, stream=None):
+    _check(lib().usr_debug_pairs(ctx, int(n), xyzq_ptr, count_ptr, hash_ptr, _stream_ptr(stream)), "usr_debug_pairs")
+
+
+def usr_set_keep_parts(ctx, on: bool):
+    _check(lib().usr_set_keep_parts(ctx, int(bool(on))), "usr_set_keep_parts")
+
+
+def usr_debug_parts(ctx, near_ptr, far_ptr, stream=None):
+    _check(lib().usr_debug_parts(ctx, near_ptr, far_ptr, _stream_ptr(stream)), "usr_debug_parts")
+
+
+def usr_set_profiling(ctx, on: bool):
+    _check(lib().usr_set_profiling(ctx, int(bool(on))), "usr_set_profiling")
+
+
+def usr_stage_times(ctx) -> Tuple[float, ...]:
+    ms = (ctypes.c_float * USR_NSTAGES)()
+    _check(lib().usr_stage_times(ctx, ms), "usr_stage_times")
+    return tuple(float(v) for v in ms)
+
+
+class USeries:
+    """One evaluation context (a usr_ctx) with torch-tensor conveniences.
+
+    xyzq: (n, 4) float32 CUDA tensor of (x, y, z, q); results are (n, 4)
+    float32 (Fx, Fy, Fz, phi) and a float64 tensor (E, E_near, E_far, E_self).
+    """
+
+    def __init__(self, box, grid, r_c, series="C1_B2", max_atoms=0, **kw):
+        self.params = make_params(box, grid, r_c, series, max_atoms=max_atoms, **kw)
+        self.ctx = usr_init(self.params)
+        self.info = usr_info(self.ctx)
+        self.max_atoms = max_atoms
+
+    def close(self):
+        if self.ctx:
+            usr_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, xyzq, out=None, energy=None, stream=None):
+        import torch
+        assert xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous() and xyzq.shape[-1] == 4
+        n = xyzq.shape[0]
+        if out is None:
+            out = torch.empty((n, 4), dtype=torch.float32, device=xyzq.device)
+        if energy is None:
+            energy = torch.empty(4, dtype=torch.float64, device=xyzq.device)
+        usr_eval(self.ctx, n, xyzq.data_ptr(), out.data_ptr(), energy.data_ptr(), stream)
+        return out, energy
+
+    def eval_host(self, xyzq, out=None, energy=None, stream=None):
+        """xyzq: (n, 4) float32 host tensor (pinned for asynchronous copies)."""
+        import torch
+        assert not xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous()
+        n = xyzq.shape[0]
+        if out is None:
+            out = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+        if energy is None:
+            energy = torch.empty(4, dtype=torch.float64, pin_memory=True)
+        usr_eval_host(self.ctx, n, xyzq.data_ptr(), out.data_ptr(), energy.data_ptr(), stream)
+        return out, energy
+
+    def debug_cells(self, xyzq):
+        import torch
+        n = xyzq.shape[0]
+        ncell = self.info.cells[0] * self.info.cells[1] * self.info.cells[2]
+        dev = xyzq.device
+        cell = torch.empty(n, dtype=torch.int32, device=dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        start = torch.empty(ncell + 1, dtype=torch.int32, device=dev)
+        xw = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        usr_debug_cells(self.ctx, n, xyzq.data_ptr(), cell.data_ptr(), perm.data_ptr(), start.data_ptr(),
+                        xw.data_ptr())
+        return cell, perm, start, xw
+
+    def debug_pairs(self, xyzq):
+        import torch
+        n = xyzq.shape[0]
+        count = torch.empty(n, dtype=torch.int32, device=xyzq.device)
+        h = torch.empty(n, dtype=torch.int64, device=xyzq.device)
+        usr_debug_pairs(self.ctx, n, xyzq.data_ptr(), count.data_ptr(), h.data_ptr())
+        return count, h
+
+    def parts(self, n):
+        import torch
+        near = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        far = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        usr_debug_parts(self.ctx, near.data_ptr(), far.data_ptr())
+        return near, far

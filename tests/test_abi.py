@@ -1,0 +1,94 @@
+"""The C ABI without a GPU: the library builds and loads, exports every entry
+point include/usr.h declares, and its host-side planning agrees with the
+paper and the oracle (no kernel is launched here)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import series as S
+from paper_1911_01377_gb300 import build as B
+from paper_1911_01377_gb300 import usr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libusr():
+    B.build()
+    return usr.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "usr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(usr_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(libusr):
+    names = _declared()
+    assert "usr_eval" in names and "usr_init" in names
+    for name in names:
+        assert hasattr(libusr, name), name
+
+
+def test_presets_are_the_paper_tables(libusr, tables):
+    keys = ["table2_C0", "table2_C1", "table2_C2", "table1_a", "table1_b", "table1_c"]
+    for pid, key in enumerate(keys):
+        s = usr.usr_series_preset(pid)
+        b, r0, w0, s0 = tables[key]
+        assert (s.b, s.r0, s.w0, s.s0) == (b, r0, w0, s0)
+        assert s.n_terms == 0 and s.trunc_eps == 0.0
+    with pytest.raises(usr.UsrError):
+        usr.usr_series_preset(6)
+
+
+@pytest.mark.parametrize("r_c", [8.0, 9.0, 10.0, 13.0])
+def test_plan_matches_closed_forms(libusr, tables, r_c):
+    box, grid = (80.0, 80.0, 100.0), (64, 64, 80)
+    info = usr.usr_plan(usr.make_params(box, grid, r_c, "C1_B2", max_atoms=10))
+    ser = O.Series(*tables["table2_C1"])
+    assert abs(info.sigma - r_c / ser.r0) < 1e-14 * info.sigma
+    assert abs(info.F0 / O.F0(ser, r_c) - 1.0) < 1e-13
+    # Eq. 33: smallest N with the bound below 1e-9
+    N = next(N for N in range(1, 17) if S.trunc_bound(N, ser.b, r_c / ser.r0, max(box)) <= 1e-9)
+    assert info.n_terms == N
+    assert abs(info.trunc_bound / S.trunc_bound(N, ser.b, r_c / ser.r0, max(box)) - 1.0) < 1e-9
+    assert list(info.cells) == [int(math.floor(L / r_c)) for L in box]
+    assert list(info.h) == [L / n for L, n in zip(box, grid)]
+    assert info.poly_max_err < 1e-9
+
+
+def test_plan_rejects_unsupported_input(libusr):
+    ok = dict(box=(31.0, 31.0, 31.0), grid=(32, 32, 32), r_c=9.0, series="C1_B2")
+    usr.usr_plan(usr.make_params(**ok))
+    bad = [dict(ok, r_c=11.0),                    # fewer than 3 cells on an axis
+           dict(ok, r_c=-1.0),
+           dict(ok, grid=(32, 16, 32)),           # fewer than spread_points + 8 points
+           dict(ok, box=(31.0, 0.0, 31.0)),
+           dict(ok, spread_sigma_over_h=3.5)]     # sigma_0^2 <= 2 sigma_s^2
+    for kw in bad:
+        with pytest.raises(usr.UsrError) as e:
+            usr.usr_plan(usr.make_params(**kw))
+        assert e.value.code == 2
+    for kw in [dict(ok, spread_points=7), dict(ok, spread_points=18), dict(ok, conv=5),
+               dict(ok, series=(0.9, 2.0, 1.0, 1.0))]:
+        with pytest.raises(usr.UsrError) as e:
+            usr.usr_plan(usr.make_params(**kw))
+        assert e.value.code == 1
+    assert usr.usr_status_string(0) == "ok"
+    assert "capacity" in usr.usr_status_string(7)
+
+
+def test_init_without_gpu_fails_cleanly(libusr):
+    # with no usable device the context cannot be created; the error is a
+    # status code, not a crash (on a GPU machine this creates a context)
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(usr.UsrError) as e:
+        usr.usr_init(usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=100))
+    assert e.value.code in (4, 5)
