@@ -49,7 +49,8 @@ typedef enum {
     USR_ERR_CUDA = 4,       /* a CUDA runtime call failed */
     USR_ERR_OOM = 5,        /* device memory allocation failed */
     USR_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
-    USR_ERR_CAPACITY = 7    /* more atoms than the context was created for */
+    USR_ERR_CAPACITY = 7,   /* more atoms than the context was created for */
+    USR_ERR_INTERNAL = 8    /* a device-side consistency check failed (a library bug; results invalid) */
 } usr_status;
 
 /* Arithmetic of the per-axis far-part convolutions. */
@@ -115,8 +116,10 @@ usr_status usr_series_preset(int preset, usr_series* out);
  * Validate parameters and derive the plan without touching the GPU.
  * USR_ERR_BOX when: any L, grid or r_c is non-positive; fewer than 3 cells
  * per axis (r_c > L/3); a grid axis has fewer than spread_points + 8 points;
- * or the narrowest kept Gaussian is not wider than sqrt(2) sigma_s (Eq. 32's
- * deconvolved widths sqrt(sigma_j^2 - 2 sigma_s^2) must be real).
+ * the narrowest kept Gaussian is not wider than sqrt(2) sigma_s (Eq. 32's
+ * deconvolved widths sqrt(sigma_j^2 - 2 sigma_s^2) must be real); or one
+ * cell's spreading tile would exceed 200 KB of shared memory (cells of more
+ * than about 30 grid points per side).
  * USR_ERR_ARG for null pointers or out-of-range series/stencil values.
  */
 usr_status usr_plan(const usr_params* p, usr_plan_info* out);
@@ -156,8 +159,8 @@ usr_status usr_eval_host(usr_ctx* ctx, int n, const float* xyzq, float* out, dou
 
 /*
  * Synchronise the context's last stream and return the device status of the
- * evaluations since the previous call (USR_OK or USR_ERR_NONFINITE), then
- * clear it.
+ * evaluations since the previous call (USR_OK, USR_ERR_NONFINITE or
+ * USR_ERR_INTERNAL), then clear it.
  */
 usr_status usr_last_device_status(usr_ctx* ctx);
 

@@ -59,42 +59,51 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
     wpos[i] = make_float4(xw, yw, zw, (ok && isfinite(p.w)) ? p.w : 0.0f);
 }
 
-/* Exclusive scan of count[0..ncell) into start[0..ncell], one block of 1024 threads. */
-__global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict__ count, int* __restrict__ start)
+/*
+ * Exclusive scans of count[0..ncell) into start[0..ncell] and of the counts
+ * rounded up to a multiple of 8 into pstart[0..ncell] (the padded 8-atom
+ * cluster layout of the pair kernel), one block of 1024 threads.
+ */
+__global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict__ count, int* __restrict__ start,
+                                               int* __restrict__ pstart)
 {
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int2 warp_sums[32];
+    __shared__ int2 carry;
+    if (threadIdx.x == 0) carry = make_int2(0, 0);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int base = 0; base < ncell; base += 1024) {
         int i = base + threadIdx.x;
         int v = i < ncell ? count[i] : 0;
-        int x = v;
+        int vp = (v + 7) & ~7;
+        int x = v, xp = vp;
         #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            int yp = __shfl_up_sync(0xffffffffu, xp, o);
+            if (lane >= o) { x += y; xp += yp; }
         }
-        if (lane == 31) warp_sums[wid] = x;
+        if (lane == 31) warp_sums[wid] = make_int2(x, xp);
         __syncthreads();
         if (wid == 0) {
-            int w = warp_sums[lane];
+            int2 w = warp_sums[lane];
             #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
+                int y = __shfl_up_sync(0xffffffffu, w.x, o);
+                int yp = __shfl_up_sync(0xffffffffu, w.y, o);
+                if (lane >= o) { w.x += y; w.y += yp; }
             }
             warp_sums[lane] = w;   // inclusive
         }
         __syncthreads();
-        int incl = x + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
-        if (i < ncell) start[i] = incl - v;
+        int2 pre = wid > 0 ? warp_sums[wid - 1] : make_int2(0, 0);
+        int incl = x + pre.x + carry.x, inclp = xp + pre.y + carry.y;
+        if (i < ncell) { start[i] = incl - v; pstart[i] = inclp - vp; }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = incl;
+        if (threadIdx.x == 1023) carry = make_int2(incl, inclp);
         __syncthreads();
     }
-    if (threadIdx.x == 0) start[ncell] = carry;
+    if (threadIdx.x == 0) { start[ncell] = carry.x; pstart[ncell] = carry.y; }
 }
 
 __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
@@ -123,14 +132,86 @@ __global__ void __launch_bounds__(256) k_cell_sort(int ncell, const int* __restr
     }
 }
 
+/*
+ * 8-atom clusters for the pair kernel, one warp per cell: the cell's atoms
+ * are ordered by the Morton code of their position on an 8 x 8 x 8 lattice
+ * inside the cell (ties by sorted index), so that runs of 8 are compact;
+ * written to the padded layout at pstart[c] with dummy rows (q = 0, far
+ * away, index -1) after the last atom; then each cluster's bounding box.
+ */
+__device__ __forceinline__ int spread3(int v)
+{
+    return (v & 1) | ((v & 2) << 2) | ((v & 4) << 4);
+}
+
+__global__ void __launch_bounds__(256) k_cluster_build(int ncell, const int* __restrict__ start,
+                                                       const int* __restrict__ pstart, const float4* __restrict__ spos,
+                                                       BoxF b, int* __restrict__ key, float4* __restrict__ cpos,
+                                                       int* __restrict__ cidx, int* __restrict__ ccell,
+                                                       float4* __restrict__ bblo, float4* __restrict__ bbhi)
+{
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const int lane = threadIdx.x & 31;
+    const int s0 = start[c], m = start[c + 1] - s0;
+    const int p0 = pstart[c], pm = pstart[c + 1] - p0;
+    const int cx = c % b.nc[0], cy = (c / b.nc[0]) % b.nc[1], cz = c / (b.nc[0] * b.nc[1]);
+    const float ox = (float)cx / b.cs[0], oy = (float)cy / b.cs[1], oz = (float)cz / b.cs[2];
+    const float kx = 8.0f * b.cs[0], ky = 8.0f * b.cs[1], kz = 8.0f * b.cs[2];
+    for (int e = lane; e < m; e += 32) {
+        const float4 p = spos[s0 + e];
+        int ix = min(7, max(0, (int)((p.x - ox) * kx)));
+        int iy = min(7, max(0, (int)((p.y - oy) * ky)));
+        int iz = min(7, max(0, (int)((p.z - oz) * kz)));
+        key[s0 + e] = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+    }
+    __syncwarp();
+    for (int e = lane; e < m; e += 32) {
+        const int ke = key[s0 + e];
+        int r = 0;
+        for (int f = 0; f < m; ++f) {
+            const int kf = key[s0 + f];
+            r += (kf < ke) || (kf == ke && f < e);
+        }
+        cpos[p0 + r] = spos[s0 + e];
+        cidx[p0 + r] = s0 + e;
+    }
+    for (int e = m + lane; e < pm; e += 32) {
+        cpos[p0 + e] = make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.0f);
+        cidx[p0 + e] = -1;
+    }
+    __syncwarp();
+    for (int k = lane; k < (pm >> 3); k += 32) {
+        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f), hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+        for (int t = 0; t < 8; ++t) {
+            const int sl = p0 + 8 * k + t;
+            if (cidx[sl] < 0) continue;
+            const float4 p = cpos[sl];
+            lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+            hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+        }
+        const int cl = (p0 >> 3) + k;
+        bblo[cl] = lo;
+        bbhi[cl] = hi;
+        ccell[cl] = c;
+    }
+}
+
+void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
+                     int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st)
+{
+    k_cluster_build<<<(ncell + 7) / 8, 256, 0, st>>>(ncell, cell_start, pstart, spos, b, key, cpos, cidx, ccell,
+                                                      bblo, bbhi);
+}
+
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                float4* wpos, int* cell_start, int* unsorted, int* perm, float4* spos, int* status,
+                float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
                 cudaStream_t st)
 {
     cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
     int nb = (n + 255) / 256;
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
-    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start);
+    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
     k_cell_sort<<<(ncell + 7) / 8, 256, 0, st>>>(ncell, cell_start, unsorted, wpos, perm, spos);
 }

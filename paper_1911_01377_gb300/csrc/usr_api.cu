@@ -29,6 +29,10 @@ struct usr_ctx {
     int *d_count = nullptr, *d_cell_of = nullptr, *d_slot = nullptr, *d_cell_start = nullptr;
     int *d_unsorted = nullptr, *d_perm = nullptr, *d_status = nullptr;
     float4 *d_wpos = nullptr, *d_spos = nullptr, *d_near = nullptr;
+    // 8-atom clusters of the pair kernel (padded layout)
+    int max_clusters = 0;
+    int *d_pstart = nullptr, *d_cidx = nullptr, *d_ccell = nullptr;
+    float4 *d_cpos = nullptr, *d_bblo = nullptr, *d_bbhi = nullptr;
     // grids and convolution tables
     float *d_rho = nullptr, *d_X = nullptr, *d_Y = nullptr, *d_psi = nullptr;
     float *d_Bx = nullptr, *d_Ay = nullptr, *d_Az = nullptr, *d_wx = nullptr, *d_wy = nullptr, *d_wz = nullptr;
@@ -65,6 +69,7 @@ usr_status dalloc(T** p, size_t count)
 void free_all(usr_ctx* c)
 {
     void* ptrs[] = {c->d_count, c->d_cell_of, c->d_slot, c->d_cell_start, c->d_unsorted, c->d_perm, c->d_status,
+                    c->d_pstart, c->d_cidx, c->d_ccell, c->d_cpos, c->d_bblo, c->d_bbhi,
                     c->d_wpos, c->d_spos, c->d_near, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
                     c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg};
@@ -147,18 +152,20 @@ void fill_args(usr_ctx* c)
     g.F0 = (float)P.F0;
 }
 
-int spread_blocks(const Plan& P)
-{
-    int nb = 1;
-    for (int a = 0; a < 3; ++a) nb *= (P.n[a] + usr::kBrick - 1) / usr::kBrick;
-    return nb;
-}
-
 usr_status check_device(const usr_ctx* c)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return USR_ERR_CUDA;
     return dev == c->device ? USR_OK : USR_ERR_ARG;
+}
+
+/* Cell list (canonical sorted order) and the 8-atom clusters built from it. */
+void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
+{
+    usr::launch_bin(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos, c->d_cell_start,
+                    c->d_pstart, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    usr::launch_clusters(c->ncell, c->d_cell_start, c->d_pstart, c->d_spos, c->boxf, c->d_slot, c->d_cpos,
+                         c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, st);
 }
 
 /* The evaluation sequence; xyzq/out are device pointers already checked. */
@@ -178,14 +185,13 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         if (c->prof) cudaEventRecord(c->ev[k], st);
     };
     mark(0);
-    usr::launch_bin(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos, c->d_cell_start,
-                    c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    bin_and_cluster(c, n, xyzq, st);
     mark(1);
-    const int block = (n <= 48 * c->ncell) ? 64 : 128;
-    usr::launch_near(c->ncell, block, P.poly_deg, c->d_spos, c->d_cell_start, c->near, c->d_near, st);
+    usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
+                     c->d_pstart, c->near, c->d_near, st);
     mark(2);
-    usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_rho, c->d_spread_partial, c->d_counters,
-                       c->d_mean, st);
+    usr::launch_spread(P.P, P.vec_spread, c->d_spos, c->d_cell_start, c->grid, P.tile, c->d_rho,
+                       c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
     mark(3);
     const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const long long G = c->G;
@@ -222,9 +228,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         usr::launch_conv(g, 1, st);
     }
     mark(6);
-    usr::launch_gather(P.P, n, c->d_spos, c->d_perm, c->d_near, c->d_psi, c->grid, out,
+    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, P.tile, out,
                        c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
-                       c->d_gather_partial, c->d_counters + 1, en, st);
+                       c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
     mark(7);
     usr_status s = check_launch();
     if (s == USR_OK) {
@@ -259,13 +265,20 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     c->G = (long long)P.n[0] * P.n[1] * P.n[2];
     const size_t na = (size_t)(c->max_atoms > 0 ? c->max_atoms : 1);
     const size_t N = (size_t)P.N;
-    const int nsb = spread_blocks(P);
-    const int ngb = usr::gather_blocks(c->max_atoms > 0 ? c->max_atoms : 1);
+    const int nsb = usr::tile_blocks(P.tile);
+    const int ngb = nsb;
     fill_args(c);
 #define ALLOC(ptr, cnt) \
     if ((s = dalloc(&(ptr), (cnt))) != USR_OK) { free_all(c); delete c; return s; }
     ALLOC(c->d_count, (size_t)c->ncell);
     ALLOC(c->d_cell_start, (size_t)c->ncell + 1);
+    c->max_clusters = (int)((na + 7 * (size_t)c->ncell + 7) / 8);
+    ALLOC(c->d_pstart, (size_t)c->ncell + 1);
+    ALLOC(c->d_cpos, (size_t)c->max_clusters * 8);
+    ALLOC(c->d_cidx, (size_t)c->max_clusters * 8);
+    ALLOC(c->d_ccell, (size_t)c->max_clusters);
+    ALLOC(c->d_bblo, (size_t)c->max_clusters);
+    ALLOC(c->d_bbhi, (size_t)c->max_clusters);
     ALLOC(c->d_cell_of, na);
     ALLOC(c->d_slot, na);
     ALLOC(c->d_unsorted, na);
@@ -300,6 +313,11 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
         free_all(c);
         delete c;
         return USR_ERR_CUDA;
+    }
+    if ((s = usr::grid_kernel_setup(P.P, usr::tile_bytes(P.tile))) != USR_OK) {
+        free_all(c);
+        delete c;
+        return s;
     }
     if ((s = upload_tables(c)) != USR_OK) {
         free_all(c);
@@ -369,7 +387,8 @@ extern "C" usr_status usr_last_device_status(usr_ctx* c)
     int v = 0;
     if (cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return USR_ERR_CUDA;
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return USR_ERR_CUDA;
-    return (v & 1) ? USR_ERR_NONFINITE : USR_OK;
+    if (v & 1) return USR_ERR_NONFINITE;
+    return (v & 2) ? USR_ERR_INTERNAL : USR_OK;
 }
 
 extern "C" usr_status usr_debug_cells(usr_ctx* c, int n, const float* xyzq, int* cell, int* perm, int* cell_start,
@@ -382,8 +401,7 @@ extern "C" usr_status usr_debug_cells(usr_ctx* c, int n, const float* xyzq, int*
     if (s != USR_OK) return s;
     if (n == 0) return USR_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    usr::launch_bin(n, (const float4*)xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
-                    c->d_cell_start, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
+    bin_and_cluster(c, n, (const float4*)xyzq, st);
     cudaMemcpyAsync(cell, c->d_cell_of, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(perm, c->d_perm, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(cell_start, c->d_cell_start, sizeof(int) * ((size_t)c->ncell + 1), cudaMemcpyDeviceToDevice, st);
@@ -399,10 +417,9 @@ extern "C" usr_status usr_debug_pairs(usr_ctx* c, int n, const float* xyzq, int*
     if (s != USR_OK) return s;
     if (n == 0) return USR_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    usr::launch_bin(n, (const float4*)xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
-                    c->d_cell_start, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
-    usr::launch_pairs(c->ncell, c->d_spos, c->d_cell_start, c->d_perm, c->near, count,
-                      (unsigned long long*)hash, st);
+    bin_and_cluster(c, n, (const float4*)xyzq, st);
+    usr::launch_pairs(c->max_clusters, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_pstart, c->d_perm,
+                      c->near, count, (unsigned long long*)hash, st);
     return check_launch();
 }
 

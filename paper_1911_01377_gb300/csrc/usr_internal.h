@@ -17,7 +17,15 @@ namespace usr {
 constexpr int kMaxPolyDeg = 24;
 constexpr int kMaxExplicit = 8;
 constexpr int kMaxTerms = 16;
-constexpr int kBrick = 8;           // spreading/interpolation brick edge (grid points)
+constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
+
+/* Cell blocks of the spreading / interpolation kernels and their smem tiles. */
+struct TileGeom {
+    int kb[3];      // cells per block per axis
+    int nbk[3];     // blocks per axis
+    int T[3];       // tile extent per axis (grid points); T[0] % 4 == 0
+    float wg[3];    // cell width in grid points, n / nc
+};
 
 /* Host plan: everything usr_init derives from usr_params, in FP64. */
 struct Plan {
@@ -43,6 +51,8 @@ struct Plan {
     double mu[3][kMaxTerms];
     double scale[kMaxTerms];
     int cells[3];
+    TileGeom tile;
+    bool vec_spread;                     // grid x extent divisible by 4: float4 reductions
 };
 
 /* Build the plan (host only).  Returns USR_OK or an error. */
@@ -89,18 +99,24 @@ struct ConvGemm {
 
 // ---- launchers (all enqueue on `st`) ----
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                float4* wpos, int* cell_start, int* unsorted, int* perm, float4* spos, int* status,
+                float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
                 cudaStream_t st);
-void launch_near(int ncell, int block, int deg, const float4* spos, const int* cell_start,
-                 const NearArgs& a, float4* out, cudaStream_t st);
-void launch_pairs(int ncell, const float4* spos, const int* cell_start, const int* perm, const NearArgs& a,
-                  int* count, unsigned long long* hash, cudaStream_t st);
-void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* rho,
-                   double* partial, unsigned int* counter, double* mean, cudaStream_t st);
+void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
+                     int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st);
+void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
+                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st);
+void launch_pairs(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
+                  const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, int* count,
+                  unsigned long long* hash, cudaStream_t st);
+void launch_spread(int P, bool vec, const float4* spos, const int* cell_start, const GridArgs& g, const TileGeom& tg,
+                   float* rho, double* partial, unsigned int* counter, double* mean, int* status, cudaStream_t st);
 void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
-void launch_gather(int P, int n, const float4* spos, const int* perm, const float4* near_out, const float* psi,
-                   const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg, double* partial,
-                   unsigned int* counter, double* energy, cudaStream_t st);
-int gather_blocks(int n);
+void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const float4* near_out,
+                   const float* psi, const GridArgs& g, const TileGeom& tg, float4* out, float4* near_dbg,
+                   float4* far_dbg, double* partial, unsigned int* counter, double* energy, int* status,
+                   cudaStream_t st);
+int tile_blocks(const TileGeom& tg);
+size_t tile_bytes(const TileGeom& tg);
+usr_status grid_kernel_setup(int P, size_t bytes);
 
 }  // namespace usr

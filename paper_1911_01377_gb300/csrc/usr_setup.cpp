@@ -186,7 +186,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
         P.L[a] = p.box[a];
         P.n[a] = p.grid[a];
         P.h[a] = p.box[a] / p.grid[a];
-        if (p.grid[a] < Pst + kBrick) return USR_ERR_BOX;
+        if (p.grid[a] < Pst + kGridMargin) return USR_ERR_BOX;
         int nc = (int)std::floor(p.box[a] / p.r_c);
         if (nc < 3) return USR_ERR_BOX;
         P.cells[a] = std::min(nc, 512);
@@ -241,13 +241,51 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             ++P.n_explicit;
         }
     }
-    static const int kDegs[] = {8, 12, 16, 20, 24};
+    // cell blocks of the spreading / interpolation kernels: cores of about 13
+    // grid points, at least 256 blocks when the cell list allows, tiles <= 100 KB
+    {
+        TileGeom& tg = P.tile;
+        auto extent = [&](int a, int kb) {
+            const double wg = (double)P.n[a] / P.cells[a];
+            int T = (int)std::ceil(kb * wg - 1e-9) + P.P + 3;
+            if (a == 0) T = ((T + 3 + 3) / 4) * 4;
+            return T;
+        };
+        auto nblocks = [&]() {
+            int nb = 1;
+            for (int a = 0; a < 3; ++a) nb *= (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
+            return nb;
+        };
+        auto bytes = [&]() { return 4.0 * extent(0, tg.kb[0]) * extent(1, tg.kb[1]) * extent(2, tg.kb[2]); };
+        for (int a = 0; a < 3; ++a) {
+            const double wg = (double)P.n[a] / P.cells[a];
+            tg.kb[a] = std::max(1, std::min(P.cells[a], (int)std::floor(13.0 / wg)));
+        }
+        auto shrink = [&]() {
+            int best = -1;
+            for (int a = 2; a >= 0; --a)
+                if (tg.kb[a] > 1 && (best < 0 || tg.kb[a] > tg.kb[best])) best = a;
+            if (best < 0) return false;
+            --tg.kb[best];
+            return true;
+        };
+        while (nblocks() < 256 && shrink()) {}
+        while (bytes() > 100.0 * 1024 && shrink()) {}
+        if (bytes() > 200.0 * 1024) return USR_ERR_BOX;
+        for (int a = 0; a < 3; ++a) {
+            tg.nbk[a] = (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
+            tg.T[a] = extent(a, tg.kb[a]);
+            tg.wg[a] = (float)((double)P.n[a] / P.cells[a]);
+        }
+        P.vec_spread = (P.n[0] % 4) == 0;
+    }
+    static const int kDegs[] = {8, 10, 12, 16, 20, 24};
     P.poly_deg = 0;
     double ev = 1.0, ed = 1.0;
     for (int D : kDegs) {
         fit_poly(P, D, P.poly, &ev, &ed);
         P.poly_deg = D;
-        if (ev < 2e-9 && ed < 2e-8) break;
+        if (ev < 1e-10 && ed < 1e-8) break;
     }
     for (int i = P.poly_deg + 1; i <= kMaxPolyDeg; ++i) P.poly[i] = 0.0;
 
@@ -301,6 +339,7 @@ extern "C" const char* usr_status_string(usr_status s)
         case USR_ERR_OOM: return "device out of memory";
         case USR_ERR_TIMEOUT: return "device wait timed out";
         case USR_ERR_CAPACITY: return "more atoms than the context capacity";
+        case USR_ERR_INTERNAL: return "internal consistency check failed";
     }
     return "unknown status";
 }
