@@ -189,6 +189,33 @@ usr_status usr_debug_cells(usr_ctx* ctx, int n, const float* xyzq, int* cell, in
 usr_status usr_debug_pairs(usr_ctx* ctx, int n, const float* xyzq, int* count, uint64_t* hash,
                            void* stream);
 
+/*
+ * The cell list of usr_debug_cells without a context and without any device
+ * allocation, for callers that cannot call cudaMalloc when they need it (a
+ * host application that owns all GPU memory through a fixed pool, code that
+ * runs inside allocator callbacks or builds CUDA graphs by hand, a tool
+ * injected into another program that must not change its memory footprint).
+ * The paper has no counterpart: this is a deployment variant of the cell-list
+ * step of the near part.
+ *   box        host, 3 doubles: box side lengths (> 0)
+ *   cells      host, 3 ints: cells per axis (>= 1), at most 65,536 cells in all
+ *   xyzq       device, n rows float4 (x, y, z, q), caller order, n <= 262,144
+ *   cell, perm, cell_start, xw   device outputs, the same as usr_debug_cells
+ *              (cell_start has cells[0]*cells[1]*cells[2] + 1 ints)
+ * The counting sort's temporaries live in one fixed file-scope device array
+ * of about 6.3 MB, which every GPU that loads the library holds until the
+ * process exits.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; each call clears what must start at zero on its own
+ * stream, and calls that overlap on the GPU (unordered streams) race on it.
+ * Non-finite rows go to cell 0 as in usr_eval but are not reported.
+ * USR_ERR_CAPACITY beyond the limits above, USR_ERR_ARG for bad pointers or
+ * sizes.  Enqueued on `stream`; no host synchronisation.
+ */
+usr_status usr_cells_static(int n, const float* xyzq, const double* box, const int* cells, int* cell, int* perm,
+                            int* cell_start, float* xw, void* stream);
+
 /* Keep (on != 0) or stop keeping the near and far parts of each usr_eval. */
 usr_status usr_set_keep_parts(usr_ctx* ctx, int on);
 

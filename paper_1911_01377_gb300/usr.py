@@ -67,12 +67,15 @@ def lib():
         L.usr_status_string.restype = ctypes.c_char_p
         L.usr_debug_cells.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]
         L.usr_debug_pairs.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
+        L.usr_cells_static.argtypes = [_c_i, _c_p, ctypes.POINTER(_c_d), ctypes.POINTER(_c_i), _c_p, _c_p, _c_p,
+                                       _c_p, _c_p]
         L.usr_set_keep_parts.argtypes = [_c_p, _c_i]
         L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
         L.usr_stage_times.argtypes = [_c_p, ctypes.POINTER(ctypes.c_float)]
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_info", "usr_eval", "usr_eval_host",
-                     "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_set_keep_parts",
+                     "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
+                     "usr_set_keep_parts",
                      "usr_debug_parts", "usr_set_profiling", "usr_stage_times"):
             getattr(L, name).restype = _c_i
         _lib = L
@@ -165,6 +168,13 @@ def usr_debug_cells(ctx, n, xyzq_ptr, cell_ptr, perm_ptr, start_ptr, xw_ptr, str
 
 def usr_debug_pairs(ctx, n, xyzq_ptr, count_ptr, hash_ptr, stream=None):
     _check(lib().usr_debug_pairs(ctx, int(n), xyzq_ptr, count_ptr, hash_ptr, _stream_ptr(stream)), "usr_debug_pairs")
+
+
+def usr_cells_static(n, xyzq_ptr, box, cells, cell_ptr, perm_ptr, start_ptr, xw_ptr, stream=None):
+    b = (_c_d * 3)(*[float(v) for v in box])
+    c = (_c_i * 3)(*[int(v) for v in cells])
+    _check(lib().usr_cells_static(int(n), xyzq_ptr, b, c, cell_ptr, perm_ptr, start_ptr, xw_ptr,
+                                  _stream_ptr(stream)), "usr_cells_static")
 
 
 def usr_set_keep_parts(ctx, on: bool):
