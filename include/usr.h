@@ -53,9 +53,16 @@ typedef enum {
     USR_ERR_INTERNAL = 8    /* a device-side consistency check failed (a library bug; results invalid) */
 } usr_status;
 
-/* Arithmetic of the per-axis far-part convolutions. */
+/*
+ * Arithmetic of the per-axis far-part convolutions (Sec. V).  The split forms
+ * run on the tensor cores (tcgen05): every operand is split into a high and a
+ * low part and three products (hi*hi + hi*lo + lo*hi) are accumulated in FP32.
+ * They need every grid dimension to be a multiple of 4 (TF32X3) or 8 (BF16X3).
+ */
 typedef enum {
-    USR_CONV_FP32 = 0       /* FP32 CUDA-core GEMMs with FP32 accumulation */
+    USR_CONV_FP32 = 0,      /* FP32 CUDA-core GEMMs with FP32 accumulation */
+    USR_CONV_TF32X3 = 1,    /* tensor cores, TF32 hi/lo split operands, FP32 accumulation */
+    USR_CONV_BF16X3 = 2     /* tensor cores, BF16 hi/lo split operands, FP32 accumulation */
 } usr_conv;
 
 /* Presets: the parameter rows printed in Table 2 (b = 2) and Table 1. */
@@ -118,8 +125,9 @@ usr_status usr_series_preset(int preset, usr_series* out);
  * per axis (r_c > L/3); a grid axis has fewer than spread_points + 8 points;
  * the narrowest kept Gaussian is not wider than sqrt(2) sigma_s (Eq. 32's
  * deconvolved widths sqrt(sigma_j^2 - 2 sigma_s^2) must be real); or one
- * cell's spreading tile would exceed 200 KB of shared memory (cells of more
- * than about 30 grid points per side).
+ * cell's spreading tile would exceed 112 KB of shared memory (cells of more
+ * than about 15 grid points per side); or a split convolution form is asked
+ * for on a grid whose dimensions are not multiples of 4 (TF32X3) or 8 (BF16X3).
  * USR_ERR_ARG for null pointers or out-of-range series/stencil values.
  */
 usr_status usr_plan(const usr_params* p, usr_plan_info* out);

@@ -114,26 +114,40 @@ __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ ce
     unsorted[start[cell_of[i]] + slot[i]] = i;
 }
 
-/* One warp per cell: rank of each entry = number of smaller caller indices in the cell. */
-__global__ void __launch_bounds__(256) k_cell_sort(int ncell, const int* __restrict__ start,
-                                                   const int* __restrict__ unsorted, const float4* __restrict__ wpos,
-                                                   int* __restrict__ perm, float4* __restrict__ spos)
+/*
+ * One CTA per cell: rank of each entry = number of smaller caller indices in
+ * the cell, counted over a shared-memory copy of the cell's entries (all
+ * threads read the same element at a time: broadcast, no bank conflicts).
+ * Cells larger than the shared copy fall back to counting in global memory.
+ */
+constexpr int kSortThreads = 128;
+constexpr int kSortMax = 2048;
+
+__global__ void __launch_bounds__(kSortThreads) k_cell_sort(const int* __restrict__ start,
+                                                            const int* __restrict__ unsorted,
+                                                            const float4* __restrict__ wpos, int* __restrict__ perm,
+                                                            float4* __restrict__ spos)
 {
-    int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= ncell) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ int v[kSortMax];
+    const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
-    for (int e = lane; e < m; e += 32) {
-        int v = unsorted[s0 + e];
+    if (m == 0) return;
+    const bool in_smem = m <= kSortMax;
+    if (in_smem)
+        for (int e = threadIdx.x; e < m; e += kSortThreads) v[e] = unsorted[s0 + e];
+    __syncthreads();
+    const int* src = in_smem ? v : unsorted + s0;
+    for (int e = threadIdx.x; e < m; e += kSortThreads) {
+        const int x = src[e];
         int r = 0;
-        for (int f = 0; f < m; ++f) r += unsorted[s0 + f] < v;
-        perm[s0 + r] = v;
-        spos[s0 + r] = wpos[v];
+        for (int f = 0; f < m; ++f) r += src[f] < x;
+        perm[s0 + r] = x;
+        spos[s0 + r] = wpos[x];
     }
 }
 
 /*
- * 8-atom clusters for the pair kernel, one warp per cell: the cell's atoms
+ * 8-atom clusters for the pair kernel, one CTA per cell: the cell's atoms
  * are ordered by the Morton code of their position on an 8 x 8 x 8 lattice
  * inside the cell (ties by sorted index), so that runs of 8 are compact;
  * written to the padded layout at pstart[c] with dummy rows (q = 0, far
@@ -144,44 +158,46 @@ __device__ __forceinline__ int spread3(int v)
     return (v & 1) | ((v & 2) << 2) | ((v & 4) << 4);
 }
 
-__global__ void __launch_bounds__(256) k_cluster_build(int ncell, const int* __restrict__ start,
-                                                       const int* __restrict__ pstart, const float4* __restrict__ spos,
-                                                       BoxF b, int* __restrict__ key, float4* __restrict__ cpos,
-                                                       int* __restrict__ cidx, int* __restrict__ ccell,
-                                                       float4* __restrict__ bblo, float4* __restrict__ bbhi)
+__global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __restrict__ start,
+                                                                const int* __restrict__ pstart,
+                                                                const float4* __restrict__ spos, BoxF b,
+                                                                int* __restrict__ key, float4* __restrict__ cpos,
+                                                                int* __restrict__ cidx, int* __restrict__ ccell,
+                                                                float4* __restrict__ bblo, float4* __restrict__ bbhi)
 {
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= ncell) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ int ks[kSortMax];
+    const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
     const int p0 = pstart[c], pm = pstart[c + 1] - p0;
     const int cx = c % b.nc[0], cy = (c / b.nc[0]) % b.nc[1], cz = c / (b.nc[0] * b.nc[1]);
     const float ox = (float)cx / b.cs[0], oy = (float)cy / b.cs[1], oz = (float)cz / b.cs[2];
     const float kx = 8.0f * b.cs[0], ky = 8.0f * b.cs[1], kz = 8.0f * b.cs[2];
-    for (int e = lane; e < m; e += 32) {
+    const bool in_smem = m <= kSortMax;
+    int* kk = in_smem ? ks : key + s0;
+    for (int e = threadIdx.x; e < m; e += kSortThreads) {
         const float4 p = spos[s0 + e];
         int ix = min(7, max(0, (int)((p.x - ox) * kx)));
         int iy = min(7, max(0, (int)((p.y - oy) * ky)));
         int iz = min(7, max(0, (int)((p.z - oz) * kz)));
-        key[s0 + e] = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+        kk[e] = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
     }
-    __syncwarp();
-    for (int e = lane; e < m; e += 32) {
-        const int ke = key[s0 + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < m; e += kSortThreads) {
+        const int ke = kk[e];
         int r = 0;
         for (int f = 0; f < m; ++f) {
-            const int kf = key[s0 + f];
+            const int kf = kk[f];
             r += (kf < ke) || (kf == ke && f < e);
         }
         cpos[p0 + r] = spos[s0 + e];
         cidx[p0 + r] = s0 + e;
     }
-    for (int e = m + lane; e < pm; e += 32) {
+    for (int e = m + threadIdx.x; e < pm; e += kSortThreads) {
         cpos[p0 + e] = make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.0f);
         cidx[p0 + e] = -1;
     }
-    __syncwarp();
-    for (int k = lane; k < (pm >> 3); k += 32) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < (pm >> 3); k += kSortThreads) {
         float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f), hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
         for (int t = 0; t < 8; ++t) {
             const int sl = p0 + 8 * k + t;
@@ -200,8 +216,7 @@ __global__ void __launch_bounds__(256) k_cluster_build(int ncell, const int* __r
 void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
                      int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st)
 {
-    k_cluster_build<<<(ncell + 7) / 8, 256, 0, st>>>(ncell, cell_start, pstart, spos, b, key, cpos, cidx, ccell,
-                                                      bblo, bbhi);
+    k_cluster_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, spos, b, key, cpos, cidx, ccell, bblo, bbhi);
 }
 
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
@@ -213,7 +228,7 @@ void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count,
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
-    k_cell_sort<<<(ncell + 7) / 8, 256, 0, st>>>(ncell, cell_start, unsorted, wpos, perm, spos);
+    k_cell_sort<<<ncell, kSortThreads, 0, st>>>(cell_start, unsorted, wpos, perm, spos);
 }
 
 }  // namespace usr

@@ -1,18 +1,22 @@
 /*
  * k_grid.cu -- the particle-grid legs of the far part (Sec. V with Gaussian
- * spreading, the GSE scheme named in Sec. IV.A).  Both kernels work on
- * blocks of cells: one CTA owns kb_x x kb_y x kb_z cells of the cell list and
- * a shared-memory tile of grid points that covers the P^3 stencils of all
- * their atoms (core + halo, T_x x T_y x T_z points, periodic wrap applied
- * when the tile meets global memory).
+ * spreading, the GSE scheme named in Sec. IV.A), atomic-free and
+ * deterministic.  Both grid kernels work on blocks of cells: one CTA owns
+ * kb_x x kb_y x kb_z cells of the sorted cell list and a shared-memory tile of
+ * grid points covering the P^3 stencils of all their atoms.
  *
- *   spread   rho_g = sum_i q_i exp(-|g - r_i|^2 / (2 sigma_s^2)) (normalisation is
- *            folded into the convolution scale).  One warp per atom adds its
- *            full stencil into the tile with shared-memory atomics; the tile is
- *            then added to the global grid with vector reductions (float4 where
- *            the x rows are 16-byte aligned).  Each CTA also reports the sum of
- *            its tile; the last CTA forms the grid mean (the k = 0 mode,
- *            dropped per Eq. 4).
+ *   spread   rho_g = sum_i q_i exp(-|g - r_i|^2 / (2 sigma_s^2)) (normalisation
+ *            folded into the convolution scale).  The CTA's warps own disjoint
+ *            sets of tile rows (y = warp mod 8) and every warp walks the
+ *            block's atoms in sorted order, adding the stencil columns of its
+ *            rows (one lane per column, all P planes) with plain shared-memory
+ *            read-modify-writes: no atomics, and every tile point receives its
+ *            terms in a fixed order.  The
+ *            tile is stored whole to a tile buffer, and the block's tile sum
+ *            is kept; the last CTA forms the grid mean (the k = 0 mode,
+ *            dropped per Eq. 4) from those sums in block order.
+ *   reduce   one thread per grid point adds the tiles that hold it, in block
+ *            order, and subtracts the grid mean.
  *   gather   phi_far,i = sum_g w(g - r_i) psi_g and F_far,i = -q_i grad phi_far,i
  *            (the second spreading Gaussian of Eq. 32's 1/|S(k)|^2).  The CTA
  *            stages its psi tile in shared memory; one warp per atom contracts
@@ -20,11 +24,19 @@
  *            part and the self term -F(0) q_i, writes (F, phi) in caller order
  *            and reduces E = 1/2 sum q_i phi_i and its parts in FP64.
  */
+#include <cuda_bf16.h>
+
 #include "usr_internal.h"
 
 namespace usr {
 
 namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 64;          // atoms whose weights are staged at once (spread)
+constexpr int kGChunk = 128;        // atoms staged at once (gather)
+constexpr int kMaxRows = 64;        // (cz, cy) rows of cells per block
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
@@ -40,124 +52,163 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-__device__ __forceinline__ int wrap_mod(int v, int n)
+/* Periodic wrap of a grid index that lies within two periods of [0, n). */
+__device__ __forceinline__ int wrap_once(int v, int n)
 {
-    v %= n;
-    return v < 0 ? v + n : v;
+    if (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
 }
 
-/* Cell block of this CTA and its tile origin (grid index of tile point 0). */
+/* Block coordinates, cell range and tile origin of CTA `bid`. */
 struct BlockGeom {
-    int c0[3], c1[3];   // cell range [c0, c1) per axis
-    int o[3];           // tile origin per axis
+    int c0[3], c1[3];
+    int o[3];
 };
 
-__device__ __forceinline__ BlockGeom block_geom(const GridArgs& g, const TileGeom& tg, int bid, int H, bool align4)
+__device__ __forceinline__ BlockGeom block_geom(const GridArgs& g, int bid)
 {
     BlockGeom b;
-    const int bx = bid % tg.nbk[0], by = (bid / tg.nbk[0]) % tg.nbk[1], bz = bid / (tg.nbk[0] * tg.nbk[1]);
-    const int bc[3] = {bx, by, bz};
+    const int nb0 = g.tg.nbk[0], nb1 = g.tg.nbk[1];
+    const int bc[3] = {bid % nb0, (bid / nb0) % nb1, bid / (nb0 * nb1)};
     #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        b.c0[a] = bc[a] * tg.kb[a];
-        b.c1[a] = min(g.box.nc[a], b.c0[a] + tg.kb[a]);
-        int o = (int)floorf((float)b.c0[a] * tg.wg[a]) - H - 1;
-        if (a == 0 && align4) o = o - (((o % 4) + 4) % 4);
-        b.o[a] = o;
+        b.c0[a] = bc[a] * g.tg.kb[a];
+        b.c1[a] = min(g.box.nc[a], b.c0[a] + g.tg.kb[a]);
+        b.o[a] = g.tab.org[a][bc[a]];
     }
     return b;
 }
 
-}  // namespace
-
-template <int P, bool VEC>
-__global__ void __launch_bounds__(256) k_spread(const float4* __restrict__ pos, const int* __restrict__ cell_start,
-                                                GridArgs g, TileGeom tg, float* __restrict__ rho,
-                                                double* __restrict__ partial, unsigned int* __restrict__ counter,
-                                                double* __restrict__ mean, int* __restrict__ status)
+/*
+ * The block's atoms are the x-runs of its (cz, cy) cell rows, contiguous in
+ * the sorted array.  Fills rs/pre (row start, prefix count) and returns the
+ * total.  Called by all threads; thread 0 writes, then a barrier.
+ */
+__device__ int block_rows(const GridArgs& g, const BlockGeom& bg, const int* __restrict__ cell_start, int* rs,
+                          int* pre)
 {
-    constexpr int H = P / 2;
-    extern __shared__ float tile[];
-    __shared__ double red[8];
-    __shared__ int is_last;
-    const int Tx = tg.T[0], Ty = tg.T[1], Tz = tg.T[2];
-    const int TT = Tx * Ty * Tz;
-    const BlockGeom bg = block_geom(g, tg, blockIdx.x, H, VEC);
-    for (int t = threadIdx.x; t < TT; t += 256) tile[t] = 0.f;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ncx = g.box.nc[0], ncy = g.box.nc[1];
-    // atoms of the block: each x-row of cells is a contiguous range of the sorted array
-    for (int cz = bg.c0[2]; cz < bg.c1[2]; ++cz) {
-        for (int cy = bg.c0[1]; cy < bg.c1[1]; ++cy) {
+    const int ny = bg.c1[1] - bg.c0[1];
+    const int nrows = ny * (bg.c1[2] - bg.c0[2]);
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int r = 0; r < nrows; ++r) {
+            const int cz = bg.c0[2] + r / ny, cy = bg.c0[1] + r % ny;
             const int row = (cz * ncy + cy) * ncx;
-            const int as = cell_start[row + bg.c0[0]], ae = cell_start[row + bg.c1[0]];
-            for (int ai = as + warp; ai < ae; ai += 8) {
-                const float4 p = pos[ai];
-                const float pc[3] = {p.x, p.y, p.z};
-                int base[3];
-                float t[3];
-                bool ok = true;
-                #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float u = pc[a] * g.box.gs[a];
-                    const float f = floorf(u);
-                    t[a] = u - f;
-                    base[a] = (int)f - H + 1 - bg.o[a];
-                    ok = ok && base[a] >= 0 && base[a] + P <= tg.T[a];
-                }
-                if (!ok) {                       // cannot happen for in-box atoms; never write outside the tile
-                    if (lane == 0) atomicOr(status, 2);
-                    continue;
-                }
-                // z weights in registers, x/y weights per (x, y) column
-                float wz[P];
-                #pragma unroll
-                for (int k = 0; k < P; ++k) {
-                    const float d = (float)(k - H + 1) - t[2];
-                    wz[k] = __expf(-d * d * g.hh[2]);
-                }
-                for (int pb = 0; pb < P * P; pb += 32) {
-                    const int pp = pb + lane;
-                    if (pp < P * P) {
-                        const int jy = pp / P, jx = pp - jy * P;
-                        const float dx = (float)(jx - H + 1) - t[0];
-                        const float dy = (float)(jy - H + 1) - t[1];
-                        const float wxy = p.w * __expf(-(dx * dx * g.hh[0] + dy * dy * g.hh[1]));
-                        float* col = tile + ((size_t)base[2] * Ty + (base[1] + jy)) * Tx + (base[0] + jx);
-                        #pragma unroll
-                        for (int k = 0; k < P; ++k) atomicAdd(col + (size_t)k * Tx * Ty, wxy * wz[k]);
-                    }
-                }
-            }
+            const int s = cell_start[row + bg.c0[0]], e = cell_start[row + bg.c1[0]];
+            rs[r] = s;
+            pre[r] = acc;
+            acc += e - s;
         }
+        pre[nrows] = acc;
     }
     __syncthreads();
-    // add the tile into the periodic grid
-    const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
-    double local = 0.0;
-    if (VEC) {
-        const int Tx4 = Tx >> 2;
-        for (int t = threadIdx.x; t < Tx4 * Ty * Tz; t += 256) {
-            const int x4 = t % Tx4, y = (t / Tx4) % Ty, z = t / (Tx4 * Ty);
-            const float* s = tile + ((size_t)z * Ty + y) * Tx + 4 * x4;
-            const float4 v = make_float4(s[0], s[1], s[2], s[3]);
-            local += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
-                const int gx = wrap_mod(bg.o[0] + 4 * x4, n0), gy = wrap_mod(bg.o[1] + y, n1),
-                          gz = wrap_mod(bg.o[2] + z, n2);
-                atomicAdd(reinterpret_cast<float4*>(rho + ((size_t)gz * n1 + gy) * n0 + gx), v);
+    return pre[nrows];
+}
+
+/* Sorted-array index of the block's j-th atom. */
+__device__ __forceinline__ int block_atom(int j, const int* rs, const int* pre)
+{
+    int r = 0;
+    while (pre[r + 1] <= j) ++r;
+    return rs[r] + (j - pre[r]);
+}
+
+}  // namespace
+
+/* ------------------------------------------------------------------ spread */
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict__ pos,
+                                                        const int* __restrict__ cell_start, GridArgs g,
+                                                        float* __restrict__ tilebuf, double* __restrict__ partial,
+                                                        unsigned int* __restrict__ counter,
+                                                        double* __restrict__ mean, int* __restrict__ status)
+{
+    constexpr int H = P / 2;
+    static_assert(2 * P <= 32 && P <= 2 * kWarps, "two stencil rows per warp, one lane per (row, column)");
+    extern __shared__ float4 smem4[];
+    float* tile = reinterpret_cast<float*>(smem4);
+    constexpr int PA = (P + 3) & ~3;              // weight rows padded to 16 bytes
+    __shared__ __align__(16) float W[kChunk][3][PA];
+    __shared__ int B[kChunk][3];
+    __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
+    __shared__ double red[kWarps];
+    __shared__ int is_last;
+
+    const int Tx = g.tg.T[0], Ty = g.tg.T[1], Tz = g.tg.T[2];
+    const int TT = Tx * Ty * Tz;
+    const int TXY = Tx * Ty;
+    const BlockGeom bg = block_geom(g, blockIdx.x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        float4* t4 = smem4;
+        for (int t = threadIdx.x; t < (TT >> 2); t += kThreads) t4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int natoms = block_rows(g, bg, cell_start, rs, pre);   // contains a barrier
+
+    for (int c0 = 0; c0 < natoms; c0 += kChunk) {
+        const int nch = min(kChunk, natoms - c0);
+        // phase 1: per-atom 1D weights (q folded into the x weights) and tile base
+        for (int idx = threadIdx.x; idx < nch * 3 * P; idx += kThreads) {
+            const int a = idx / (3 * P), rem = idx - a * 3 * P;
+            const int ax = rem / P, k = rem - ax * P;
+            const float4 p = pos[block_atom(c0 + a, rs, pre)];
+            // per-axis constants selected without dynamic indexing (keeps them in registers)
+            const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+            const float gs = ax == 0 ? g.box.gs[0] : (ax == 1 ? g.box.gs[1] : g.box.gs[2]);
+            const float hh = ax == 0 ? g.hh[0] : (ax == 1 ? g.hh[1] : g.hh[2]);
+            const int org = ax == 0 ? bg.o[0] : (ax == 1 ? bg.o[1] : bg.o[2]);
+            const int Ta = ax == 0 ? Tx : (ax == 1 ? Ty : Tz);
+            const float u = pc * gs;
+            const float f = floorf(u);
+            const float t = u - f;
+            const float d = (float)(k - H + 1) - t;
+            float w = __expf(-d * d * hh);
+            if (ax == 0) w *= p.w;
+            W[a][ax][k] = w;
+            if (k == 0) {
+                const int base = (int)f - H + 1 - org;
+                const bool ok = base >= 0 && base + P <= Ta;
+                B[a][ax] = ok ? base : -1;
+                if (!ok) atomicOr(status, 2);    // cannot happen for wrapped positions
             }
         }
-    } else {
-        for (int t = threadIdx.x; t < TT; t += 256) {
-            const int x = t % Tx, y = (t / Tx) % Ty, z = t / (Tx * Ty);
-            const float v = tile[t];
-            local += (double)v;
-            if (v != 0.f) {
-                const int gx = wrap_mod(bg.o[0] + x, n0), gy = wrap_mod(bg.o[1] + y, n1), gz = wrap_mod(bg.o[2] + z, n2);
-                atomicAdd(rho + ((size_t)gz * n1 + gy) * n0 + gx, v);
+        __syncthreads();
+        // phase 2: warp w owns the tile rows ty = w (mod 8); for each atom it adds
+        // the stencil columns of its rows, all P planes of a column per lane
+        for (int a = 0; a < nch; ++a) {
+            const int bx = B[a][0], by = B[a][1], bz = B[a][2];
+            if (bx < 0 || by < 0 || bz < 0) continue;
+            const int jy = ((warp - by) % kWarps + kWarps) % kWarps + kWarps * (lane / P);
+            const int jx = lane % P;
+            if (lane >= 2 * P || jy >= P) continue;
+            const float v = W[a][0][jx] * W[a][1][jy];
+            float* col = tile + ((bz * Ty + by + jy) * Tx + bx + jx);
+            float wz[PA], t[P];
+            #pragma unroll
+            for (int k = 0; k < PA; k += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(&W[a][2][k]);
+                wz[k] = w4.x; wz[k + 1] = w4.y; wz[k + 2] = w4.z; wz[k + 3] = w4.w;
             }
+            #pragma unroll
+            for (int k = 0; k < P; ++k) t[k] = col[k * TXY];
+            #pragma unroll
+            for (int k = 0; k < P; ++k) col[k * TXY] = fmaf(v, wz[k], t[k]);
+        }
+        __syncthreads();
+    }
+
+    // store the tile, sum it in a fixed order
+    double local = 0.0;
+    {
+        const float4* t4 = smem4;
+        float4* out4 = reinterpret_cast<float4*>(tilebuf + (size_t)blockIdx.x * TT);
+        for (int t = threadIdx.x; t < (TT >> 2); t += kThreads) {
+            const float4 v = t4[t];
+            out4[t] = v;
+            local += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
         }
     }
     local = warp_sum_d(local);
@@ -165,7 +216,7 @@ __global__ void __launch_bounds__(256) k_spread(const float4* __restrict__ pos, 
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w];
+        for (int w = 0; w < kWarps; ++w) s += red[w];
         partial[blockIdx.x] = s;
         __threadfence();
         const unsigned int ticket = atomicAdd(counter, 1u);
@@ -173,122 +224,266 @@ __global__ void __launch_bounds__(256) k_spread(const float4* __restrict__ pos, 
     }
     __syncthreads();
     if (is_last) {
+        // grid mean from the block sums, in block order (the same whichever CTA is last)
         __threadfence();
         double s = 0.0;
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += 256) s += ((volatile double*)partial)[k];
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) s += ((volatile double*)partial)[k];
         s = warp_sum_d(s);
         if (lane == 0) red[warp] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
-            for (int w = 0; w < 8; ++w) tot += red[w];
-            *mean = tot / ((double)n0 * n1 * n2);
+            for (int w = 0; w < kWarps; ++w) tot += red[w];
+            *mean = tot / ((double)g.box.n[0] * g.box.n[1] * g.box.n[2]);
             *counter = 0u;
         }
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_gather(const float4* __restrict__ pos, const int* __restrict__ cell_start,
-                                                const int* __restrict__ perm, const float4* __restrict__ near_out,
-                                                const float* __restrict__ psi, GridArgs g, TileGeom tg,
-                                                float4* __restrict__ out, float4* __restrict__ near_dbg,
-                                                float4* __restrict__ far_dbg, double* __restrict__ partial,
-                                                unsigned int* __restrict__ counter, double* __restrict__ energy,
-                                                int* __restrict__ status)
+/*
+ * rho_g = (sum of the tiles holding g, in block order) - mean.  SPLIT = 0
+ * writes FP32 rho; 1 and 2 write the operand split of the tensor-core
+ * convolution instead: rho = hi + lo with hi rounded to TF32 (1) or BF16 (2).
+ */
+template <int SPLIT>
+__global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __restrict__ tilebuf,
+                                                     const double* __restrict__ mean, void* __restrict__ rho,
+                                                     void* __restrict__ rho_lo)
 {
-    constexpr int H = P / 2;
-    extern __shared__ float tile[];
-    __shared__ double red[8][4];
-    __shared__ int is_last;
-    const int Tx = tg.T[0], Ty = tg.T[1], Tz = tg.T[2];
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
-    const BlockGeom bg = block_geom(g, tg, blockIdx.x, H, false);
-    for (int t = threadIdx.x; t < Tx * Ty * Tz; t += 256) {
-        const int x = t % Tx, y = (t / Tx) % Ty, z = t / (Tx * Ty);
-        const int gx = wrap_mod(bg.o[0] + x, n0), gy = wrap_mod(bg.o[1] + y, n1), gz = wrap_mod(bg.o[2] + z, n2);
-        tile[t] = __ldg(psi + ((size_t)gz * n1 + gy) * n0 + gx);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ncx = g.box.nc[0], ncy = g.box.nc[1];
-    double e_tot = 0.0, e_near = 0.0, e_far = 0.0, e_self = 0.0;
-    for (int cz = bg.c0[2]; cz < bg.c1[2]; ++cz) {
-        for (int cy = bg.c0[1]; cy < bg.c1[1]; ++cy) {
-            const int row = (cz * ncy + cy) * ncx;
-            const int as = cell_start[row + bg.c0[0]], ae = cell_start[row + bg.c1[0]];
-            for (int s = as + warp; s < ae; s += 8) {
-                const float4 p = pos[s];
-                const float pc[3] = {p.x, p.y, p.z};
-                int base[3];
-                float t[3];
-                bool ok = true;
-                #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float u = pc[a] * g.box.gs[a];
-                    const float f = floorf(u);
-                    t[a] = u - f;
-                    base[a] = (int)f - H + 1 - bg.o[a];
-                    ok = ok && base[a] >= 0 && base[a] + P <= tg.T[a];
-                }
-                float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-                if (ok) {
-                    float wz[P], dz[P];
-                    #pragma unroll
-                    for (int k = 0; k < P; ++k) {
-                        const float d = (float)(k - H + 1) - t[2];
-                        wz[k] = __expf(-d * d * g.hh[2]);
-                        dz[k] = wz[k] * d * g.dfac[2];
-                    }
-                    for (int pb = 0; pb < P * P; pb += 32) {
-                        const int pp = pb + lane;
-                        if (pp < P * P) {
-                            const int jy = pp / P, jx = pp - jy * P;
-                            const float dx = (float)(jx - H + 1) - t[0];
-                            const float dy = (float)(jy - H + 1) - t[1];
-                            const float wx = __expf(-dx * dx * g.hh[0]);
-                            const float wy = __expf(-dy * dy * g.hh[1]);
-                            const float* col = tile + ((size_t)base[2] * Ty + (base[1] + jy)) * Tx + (base[0] + jx);
-                            float cz0 = 0.f, cz1 = 0.f;
-                            #pragma unroll
-                            for (int k = 0; k < P; ++k) {
-                                const float v = col[(size_t)k * Tx * Ty];
-                                cz0 = fmaf(wz[k], v, cz0);
-                                cz1 = fmaf(dz[k], v, cz1);
-                            }
-                            const float wxy = wx * wy;
-                            aphi = fmaf(wxy, cz0, aphi);
-                            ax = fmaf(wx * dx * g.dfac[0] * wy, cz0, ax);
-                            ay = fmaf(wx * wy * dy * g.dfac[1], cz0, ay);
-                            az = fmaf(wxy, cz1, az);
-                        }
-                    }
-                } else if (lane == 0) {
-                    atomicOr(status, 2);
-                }
-                aphi = warp_sum_f(aphi);
-                ax = warp_sum_f(ax);
-                ay = warp_sum_f(ay);
-                az = warp_sum_f(az);
-                if (lane == 0) {
-                    const int i = perm[s];
-                    const float qi = p.w;
-                    const float4 nr = near_out[s];
-                    const float fx = -qi * ax, fy = -qi * ay, fz = -qi * az;
-                    const float phi = nr.w + aphi - g.F0 * qi;
-                    out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
-                    if (near_dbg) near_dbg[i] = nr;
-                    if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
-                    const double en = 0.5 * (double)qi * (double)nr.w;
-                    const double ef = 0.5 * (double)qi * (double)aphi;
-                    const double es = -0.5 * (double)g.F0 * (double)qi * (double)qi;
-                    e_near += en;
-                    e_far += ef;
-                    e_self += es;
-                    e_tot += en + ef + es;
-                }
+    const long long G = (long long)n0 * n1 * n2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G) return;
+    const int x = (int)(idx % n0), y = (int)((idx / n0) % n1), z = (int)(idx / ((long long)n0 * n1));
+    const int T0 = g.tg.T[0], T1 = g.tg.T[1], T2 = g.tg.T[2];
+    const long long TT = (long long)T0 * T1 * T2;
+    const int nb0 = g.tg.nbk[0], nb1 = g.tg.nbk[1];
+    const int cz = g.tab.red_cnt[2][z], cy = g.tab.red_cnt[1][y], cx = g.tab.red_cnt[0][x];
+    const int2* pz = g.tab.red_pair[2] + (size_t)z * g.tg.rmax[2];
+    const int2* py = g.tab.red_pair[1] + (size_t)y * g.tg.rmax[1];
+    const int2* px = g.tab.red_pair[0] + (size_t)x * g.tg.rmax[0];
+    float s = 0.f;
+    for (int iz = 0; iz < cz; ++iz) {
+        const int2 bz = pz[iz];
+        for (int iy = 0; iy < cy; ++iy) {
+            const int2 by = py[iy];
+            const long long rowbase = ((long long)(bz.x * nb1 + by.x) * nb0) * TT + ((long long)bz.y * T1 + by.y) * T0;
+            for (int ix = 0; ix < cx; ++ix) {
+                const int2 bx = px[ix];
+                s += __ldg(tilebuf + rowbase + (long long)bx.x * TT + bx.y);
             }
         }
+    }
+    const float v = (float)((double)s - *mean);
+    if (SPLIT == 0) {
+        static_cast<float*>(rho)[idx] = v;
+    } else if (SPLIT == 1) {
+        uint32_t hb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+        const float h = __uint_as_float(hb);
+        static_cast<float*>(rho)[idx] = h;
+        static_cast<float*>(rho_lo)[idx] = v - h;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        static_cast<__nv_bfloat16*>(rho)[idx] = h;
+        static_cast<__nv_bfloat16*>(rho_lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+/*
+ * Grid mean of psi.  Exact arithmetic gives psi no k = 0 mode (rho has its
+ * mean removed and the kernels are convolutions), but the FP32 rounding of
+ * rho's mean removal leaves a tiny mean that the wide Gaussian terms amplify
+ * by their k = 0 transform; the gather subtracts the mean measured here.
+ * Fixed-order FP64 partial sums, the last CTA finishes.
+ */
+__global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __restrict__ psi,
+                                                   double* __restrict__ partial, unsigned int* __restrict__ counter,
+                                                   double* __restrict__ mean)
+{
+    __shared__ double red[8];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+        s += (double)psi[i];
+    s = warp_sum_d(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partial[blockIdx.x] = t;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double t = 0.0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += 256) t += ((volatile double*)partial)[k];
+        t = warp_sum_d(t);
+        if (lane == 0) red[warp] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double u = 0.0;
+            for (int w = 0; w < 8; ++w) u += red[w];
+            *mean = u / (double)G;
+            *counter = 0u;
+        }
+    }
+}
+
+void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
+                      cudaStream_t st)
+{
+    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
+    k_grid_mean<<<kGridMeanBlocks, 256, 0, st>>>(G, psi, partial, counter, mean);
+}
+
+/* ------------------------------------------------------------------ gather */
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict__ pos,
+                                                        const int* __restrict__ cell_start,
+                                                        const int* __restrict__ perm,
+                                                        const float4* __restrict__ near_out,
+                                                        const float* __restrict__ psi, GridArgs g,
+                                                        float4* __restrict__ out, float4* __restrict__ near_dbg,
+                                                        float4* __restrict__ far_dbg, double* __restrict__ partial,
+                                                        unsigned int* __restrict__ counter,
+                                                        double* __restrict__ energy, int* __restrict__ status)
+{
+    constexpr int H = P / 2;
+    constexpr int NIT = (P * P + 31) / 32;
+    extern __shared__ float4 smem4[];
+    float* tile = reinterpret_cast<float*>(smem4);
+    __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
+    __shared__ double red[kWarps][4];
+    __shared__ float4 sp[kGChunk], sn[kGChunk];   // staged atoms: position/charge, near part
+    __shared__ int si[kGChunk];                   // and caller index
+    __shared__ int is_last;
+    const int Tx = g.tg.T[0], Ty = g.tg.T[1], Tz = g.tg.T[2];
+    const int TXY = Tx * Ty;
+    const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
+    const BlockGeom bg = block_geom(g, blockIdx.x);
+    // stage the psi tile with asynchronous 4-byte copies (many in flight per thread)
+    for (int r = threadIdx.x >> 5; r < Ty * Tz; r += kWarps) {
+        const int ty = r % Ty, tz = r / Ty;
+        const int gy = wrap_once(bg.o[1] + ty, n1), gz = wrap_once(bg.o[2] + tz, n2);
+        const float* src = psi + ((size_t)gz * n1 + gy) * n0;
+        float* dst = tile + (size_t)r * Tx;
+        for (int tx = threadIdx.x & 31; tx < Tx; tx += 32) {
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + tx));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + wrap_once(bg.o[0] + tx, n0))
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int natoms = block_rows(g, bg, cell_start, rs, pre);   // contains a barrier
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int col_jx[NIT], col_jy[NIT], col_off[NIT];
+    #pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int pp = lane + 32 * it;
+        col_jy[it] = pp < P * P ? pp / P : -1;
+        col_jx[it] = pp < P * P ? pp - (pp / P) * P : 0;
+        col_off[it] = max(col_jy[it], 0) * Tx + col_jx[it];
+    }
+    double e_tot = 0.0, e_near = 0.0, e_far = 0.0, e_self = 0.0;
+    const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
+    for (int c0 = 0; c0 < natoms; c0 += kGChunk) {
+        const int nch = min(kGChunk, natoms - c0);
+        __syncthreads();                           // the previous chunk is done
+        for (int a = threadIdx.x; a < nch; a += kThreads) {
+            const int s = block_atom(c0 + a, rs, pre);
+            sp[a] = pos[s];
+            sn[a] = near_out[s];
+            si[a] = perm[s];
+        }
+        __syncthreads();
+    for (int j = warp; j < nch; j += kWarps) {
+        const float4 p = sp[j];
+        const float pc[3] = {p.x, p.y, p.z};
+        int base[3];
+        float wk[3], dk[3];              // lane k < P: weight and derivative factor of stencil point k
+        bool ok = true;
+        #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u = pc[a] * g.box.gs[a];
+            const float f = floorf(u);
+            const float t = u - f;
+            base[a] = (int)f - H + 1 - bg.o[a];
+            ok = ok && base[a] >= 0 && base[a] + P <= g.tg.T[a];
+            const float d = (float)(min(lane, P - 1) - H + 1) - t;
+            wk[a] = __expf(-d * d * g.hh[a]);
+            dk[a] = wk[a] * d * g.dfac[a];
+        }
+        float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+        if (ok) {
+            float wz[P], dz[P];
+            #pragma unroll
+            for (int k = 0; k < P; ++k) {
+                wz[k] = __shfl_sync(0xffffffffu, wk[2], k);
+                dz[k] = __shfl_sync(0xffffffffu, dk[2], k);
+            }
+            const float* b0 = tile + ((base[2] * Ty + base[1]) * Tx + base[0]);
+            #pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int jx = col_jx[it], jy = max(col_jy[it], 0);
+                const float wx = __shfl_sync(0xffffffffu, wk[0], jx);
+                const float dwx = __shfl_sync(0xffffffffu, dk[0], jx);
+                const float wy = __shfl_sync(0xffffffffu, wk[1], jy);
+                const float dwy = __shfl_sync(0xffffffffu, dk[1], jy);
+                if (col_jy[it] >= 0) {
+                    const float* col = b0 + col_off[it];
+                    float v[P];
+                    #pragma unroll
+                    for (int k = 0; k < P; ++k) v[k] = col[k * TXY];
+                    // two interleaved partial sums per contraction (shorter FMA chains)
+                    float c0a = 0.f, c0b = 0.f, c1a = 0.f, c1b = 0.f;
+                    #pragma unroll
+                    for (int k = 0; k < P; k += 2) {
+                        c0a = fmaf(wz[k], v[k], c0a);
+                        c1a = fmaf(dz[k], v[k], c1a);
+                        c0b = fmaf(wz[k + 1], v[k + 1], c0b);
+                        c1b = fmaf(dz[k + 1], v[k + 1], c1b);
+                    }
+                    const float cz0 = c0a + c0b, cz1 = c1a + c1b;
+                    const float wxy = wx * wy;
+                    aphi = fmaf(wxy, cz0, aphi);
+                    ax = fmaf(dwx * wy, cz0, ax);
+                    ay = fmaf(wx * dwy, cz0, ay);
+                    az = fmaf(wxy, cz1, az);
+                }
+            }
+        } else if (lane == 0) {
+            atomicOr(status, 2);          // cannot happen for wrapped positions
+        }
+        aphi = warp_sum_f(aphi) - phi_dc;
+        ax = warp_sum_f(ax);
+        ay = warp_sum_f(ay);
+        az = warp_sum_f(az);
+        if (lane == 0) {
+            const int i = si[j];
+            const float qi = p.w;
+            const float4 nr = sn[j];
+            const float fx = -qi * ax, fy = -qi * ay, fz = -qi * az;
+            const float phi = nr.w + aphi - g.F0 * qi;
+            out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
+            if (near_dbg) near_dbg[i] = nr;
+            if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
+            const double en = 0.5 * (double)qi * (double)nr.w;
+            const double ef = 0.5 * (double)qi * (double)aphi;
+            const double es = -0.5 * g.F0d * (double)qi * (double)qi;
+            e_near += en;
+            e_far += ef;
+            e_self += es;
+            e_tot += en + ef + es;
+        }
+    }
     }
     if (lane == 0) {
         red[warp][0] = e_tot;
@@ -299,7 +494,7 @@ __global__ void __launch_bounds__(256) k_gather(const float4* __restrict__ pos, 
     __syncthreads();
     if (threadIdx.x < 4) {
         double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+        for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
         partial[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
         __threadfence();
     }
@@ -312,7 +507,7 @@ __global__ void __launch_bounds__(256) k_gather(const float4* __restrict__ pos, 
     if (is_last) {
         __threadfence();
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += 256) {
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) {
             #pragma unroll
             for (int c = 0; c < 4; ++c) acc[c] += ((volatile double*)partial)[(size_t)k * 4 + c];
         }
@@ -324,27 +519,29 @@ __global__ void __launch_bounds__(256) k_gather(const float4* __restrict__ pos, 
         __syncthreads();
         if (threadIdx.x < 4) {
             double v = 0.0;
-            for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+            for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
             energy[threadIdx.x] = v;
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
 
+/* ------------------------------------------------------------------ launch */
+
 int tile_blocks(const TileGeom& tg) { return tg.nbk[0] * tg.nbk[1] * tg.nbk[2]; }
 
-size_t tile_bytes(const TileGeom& tg) { return sizeof(float) * (size_t)tg.T[0] * tg.T[1] * tg.T[2]; }
+size_t tile_floats(const TileGeom& tg) { return (size_t)tg.T[0] * tg.T[1] * tg.T[2]; }
 
 template <int P>
 static void set_smem(size_t bytes)
 {
-    cudaFuncSetAttribute(k_spread<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(k_spread<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_spread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     cudaFuncSetAttribute(k_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-usr_status grid_kernel_setup(int P, size_t bytes)
+usr_status grid_kernel_setup(int P, const TileGeom& tg)
 {
+    const size_t bytes = sizeof(float) * tile_floats(tg);
     switch (P) {
         case 8: set_smem<8>(bytes); break;
         case 10: set_smem<10>(bytes); break;
@@ -355,21 +552,17 @@ usr_status grid_kernel_setup(int P, size_t bytes)
     return cudaGetLastError() == cudaSuccess ? USR_OK : USR_ERR_CUDA;
 }
 
-#define USR_SPREAD_CASE(PP)                                                                                         \
-    case PP:                                                                                                        \
-        if (vec)                                                                                                    \
-            k_spread<PP, true><<<nb, 256, smem, st>>>(spos, cell_start, g, tg, rho, partial, counter, mean, status); \
-        else                                                                                                        \
-            k_spread<PP, false><<<nb, 256, smem, st>>>(spos, cell_start, g, tg, rho, partial, counter, mean, status); \
+#define USR_SPREAD_CASE(PP)                                                                                     \
+    case PP:                                                                                                    \
+        k_spread<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, g, tilebuf, partial, counter, mean, status); \
         break;
 
-void launch_spread(int P, bool vec, const float4* spos, const int* cell_start, const GridArgs& g, const TileGeom& tg,
-                   float* rho, double* partial, unsigned int* counter, double* mean, int* status, cudaStream_t st)
+void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
+                   void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
+                   cudaStream_t st)
 {
-    const int nb = tile_blocks(tg);
-    const size_t smem = tile_bytes(tg);
-    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
-    cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)G, st);
+    const int nb = tile_blocks(g.tg);
+    const size_t smem = sizeof(float) * tile_floats(g.tg);
     switch (P) {
         USR_SPREAD_CASE(8)
         USR_SPREAD_CASE(10)
@@ -378,21 +571,28 @@ void launch_spread(int P, bool vec, const float4* spos, const int* cell_start, c
         default:
         USR_SPREAD_CASE(16)
     }
+    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
+    const unsigned nr = (unsigned)((G + 255) / 256);
+    if (split == 1)
+        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo);
+    else if (split == 2)
+        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo);
+    else
+        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr);
 }
 
-#define USR_GATHER_CASE(PP)                                                                                     \
-    case PP:                                                                                                    \
-        k_gather<PP><<<nb, 256, smem, st>>>(spos, cell_start, perm, near_out, psi, g, tg, out, near_dbg, far_dbg, \
-                                             partial, counter, energy, status);                                 \
+#define USR_GATHER_CASE(PP)                                                                                      \
+    case PP:                                                                                                     \
+        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, perm, near_out, psi, g, out, near_dbg, far_dbg, \
+                                                  partial, counter, energy, status);                             \
         break;
 
 void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const float4* near_out,
-                   const float* psi, const GridArgs& g, const TileGeom& tg, float4* out, float4* near_dbg,
-                   float4* far_dbg, double* partial, unsigned int* counter, double* energy, int* status,
-                   cudaStream_t st)
+                   const float* psi, const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg,
+                   double* partial, unsigned int* counter, double* energy, int* status, cudaStream_t st)
 {
-    const int nb = tile_blocks(tg);
-    const size_t smem = tile_bytes(tg);
+    const int nb = tile_blocks(g.tg);
+    const size_t smem = sizeof(float) * tile_floats(g.tg);
     switch (P) {
         USR_GATHER_CASE(8)
         USR_GATHER_CASE(10)

@@ -8,9 +8,12 @@
  *   x / y / z convolution passes (Sec. V, Eqs. 31-32) -> gather + combine +
  *   FP64 energy reduction.
  */
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
+
+#include <cuda_bf16.h>
 
 #include "usr_internal.h"
 
@@ -38,6 +41,20 @@ struct usr_ctx {
     float *d_Bx = nullptr, *d_Ay = nullptr, *d_Az = nullptr, *d_wx = nullptr, *d_wy = nullptr, *d_wz = nullptr;
     double *d_spread_partial = nullptr, *d_mean = nullptr, *d_gather_partial = nullptr, *d_energy = nullptr;
     unsigned int* d_counters = nullptr;
+    double *d_psi_partial = nullptr, *d_psi_mean = nullptr;
+    // spreading tiles and the per-axis tile tables
+    float* d_tilebuf = nullptr;
+    int* d_tab[3] = {nullptr, nullptr, nullptr};
+    // tensor-core convolutions: split operands (hi, lo), B tables per pass, per-term means
+    bool tc = false, tc_bf16 = false;
+    void *d_rho_hi = nullptr, *d_rho_lo = nullptr, *d_X_hi = nullptr, *d_X_lo = nullptr;
+    void *d_Y_hi = nullptr, *d_Y_lo = nullptr;
+    void* d_Bt_hi[3] = {nullptr, nullptr, nullptr};
+    void* d_Bt_lo[3] = {nullptr, nullptr, nullptr};
+    float* d_mu = nullptr;
+    usr::ConvTcMaps maps[3];
+    usr::ConvTcArgs targs[3];
+    int tbatches[3] = {0, 0, 0};
     // host-buffer staging and inspection
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
     bool keep_parts = false;
@@ -72,7 +89,10 @@ void free_all(usr_ctx* c)
                     c->d_pstart, c->d_cidx, c->d_ccell, c->d_cpos, c->d_bblo, c->d_bbhi,
                     c->d_wpos, c->d_spos, c->d_near, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
-                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg};
+                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_tilebuf,
+                    c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_rho_hi, c->d_rho_lo, c->d_X_hi, c->d_X_lo,
+                    c->d_Y_hi, c->d_Y_lo, c->d_Bt_hi[0], c->d_Bt_hi[1], c->d_Bt_hi[2], c->d_Bt_lo[0],
+                    c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_made)
@@ -124,6 +144,189 @@ usr_status upload_tables(usr_ctx* c)
     for (auto& u : ups)
         if (cudaMemcpy(u.d, u.h->data(), sizeof(float) * u.h->size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return USR_ERR_CUDA;
+    // per axis: tile origins, then reduction counts, then (block, offset) pairs
+    for (int a = 0; a < 3; ++a) {
+        std::vector<int> t;
+        t.insert(t.end(), P.tile_org[a].begin(), P.tile_org[a].end());
+        t.insert(t.end(), P.red_cnt[a].begin(), P.red_cnt[a].end());
+        while (t.size() % 2) t.push_back(0);
+        t.insert(t.end(), P.red_pair[a].begin(), P.red_pair[a].end());
+        if (cudaMemcpy(c->d_tab[a], t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return USR_ERR_CUDA;
+        const size_t off_cnt = P.tile_org[a].size();
+        const size_t off_pair = (off_cnt + P.red_cnt[a].size() + 1) / 2 * 2;
+        c->grid.tab.org[a] = c->d_tab[a];
+        c->grid.tab.red_cnt[a] = c->d_tab[a] + off_cnt;
+        c->grid.tab.red_pair[a] = reinterpret_cast<const int2*>(c->d_tab[a] + off_pair);
+    }
+    return USR_OK;
+}
+
+size_t tab_ints(const Plan& P, int a)
+{
+    const size_t head = (P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2;
+    return head + P.red_pair[a].size();
+}
+
+/* Host round-to-nearest (ties away from zero) to TF32, as cvt.rna.tf32.f32 does. */
+float tf32_rna(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+/* Tile shape of one tensor-core pass with n_out output columns and contraction K. */
+void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16)
+{
+    a.n_out = n_out;
+    a.K = K;
+    a.ntiles = (n_out + 1 + 255) / 256;
+    a.cols = (n_out + a.ntiles - 1) / a.ntiles;
+    a.NT = ((a.cols + 1 + 15) / 16) * 16;
+    a.tmem_cols = 32;
+    while (a.tmem_cols < a.NT) a.tmem_cols *= 2;
+    const int kstage = bf16 ? 64 : 32;
+    const int nk = (K + kstage - 1) / kstage;
+    const size_t stage = (size_t)(2 * 128 + 2 * a.NT) * 128;
+    int S = (int)((200 * 1024) / stage);
+    S = std::min(S, std::min(nk, 4));
+    a.stages = std::max(1, std::min(S, usr::kConvTcMaxStages));
+}
+
+/* Split a table of doubles into hi/lo device arrays of the pass element type. */
+usr_status upload_split(const std::vector<double>& v, bool bf16, void* hi, void* lo)
+{
+    const size_t n = v.size();
+    if (bf16) {
+        std::vector<__nv_bfloat16> h(n), l(n);
+        for (size_t i = 0; i < n; ++i) {
+            h[i] = __float2bfloat16_rn((float)v[i]);
+            l[i] = __float2bfloat16_rn((float)(v[i] - (double)__bfloat162float(h[i])));
+        }
+        if (cudaMemcpy(hi, h.data(), 2 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(lo, l.data(), 2 * n, cudaMemcpyHostToDevice) != cudaSuccess)
+            return USR_ERR_CUDA;
+    } else {
+        std::vector<float> h(n), l(n);
+        for (size_t i = 0; i < n; ++i) {
+            h[i] = tf32_rna((float)v[i]);
+            l[i] = tf32_rna((float)(v[i] - (double)h[i]));
+        }
+        if (cudaMemcpy(hi, h.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(lo, l.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess)
+            return USR_ERR_CUDA;
+    }
+    return USR_OK;
+}
+
+/*
+ * B tables of the three tensor-core passes: rows [batch][tile][NT] of length
+ * K; row c < cols of tile t is output column m = t cols + c, row cols is the
+ * DC row, the rest are zero.
+ */
+std::vector<double> tc_table(const Plan& P, int pass, const usr::ConvTcArgs& a, int batches)
+{
+    const int N = P.N, nz = P.n[2];
+    std::vector<double> B((size_t)batches * a.ntiles * a.NT * a.K, 0.0);
+    for (int b = 0; b < batches; ++b)
+        for (int t = 0; t < a.ntiles; ++t)
+            for (int c = 0; c <= a.cols; ++c) {
+                double* row = B.data() + (((size_t)b * a.ntiles + t) * a.NT + c) * a.K;
+                const int m = t * a.cols + c;
+                if (c == a.cols) {                  // DC row
+                    if (pass == 3) {
+                        for (int j = 0; j < N; ++j)
+                            for (int k = 0; k < nz; ++k) row[j * nz + k] = P.scale[j] * P.mu[2][j];
+                    } else {
+                        for (int k = 0; k < a.K; ++k) row[k] = 1.0;
+                    }
+                    continue;
+                }
+                if (m >= a.n_out) continue;
+                if (pass == 3) {
+                    for (int j = 0; j < N; ++j)
+                        for (int k = 0; k < nz; ++k)
+                            row[j * nz + k] = P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz];
+                } else {
+                    const int ax = pass - 1, n = P.n[ax];
+                    for (int k = 0; k < n; ++k) row[k] = P.ktil[ax][b][((m - k) % n + n) % n];
+                }
+            }
+    return B;
+}
+
+usr_status setup_tc(usr_ctx* c)
+{
+    const Plan& P = c->plan;
+    const bool bf = c->tc_bf16;
+    const size_t es = bf ? 2 : 4;
+    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t G = (size_t)c->G;
+    auto alloc = [&](void** p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return e == cudaErrorMemoryAllocation ? USR_ERR_OOM : USR_ERR_CUDA;
+        }
+        return USR_OK;
+    };
+    usr_status s;
+    if ((s = alloc(&c->d_rho_hi, es * G)) || (s = alloc(&c->d_rho_lo, es * G)) ||
+        (s = alloc(&c->d_X_hi, es * G * N)) || (s = alloc(&c->d_X_lo, es * G * N)) ||
+        (s = alloc(&c->d_Y_hi, es * G * N)) || (s = alloc(&c->d_Y_lo, es * G * N)) ||
+        (s = alloc((void**)&c->d_mu, sizeof(float) * 2 * N)))
+        return s;
+    std::vector<float> mu(2 * N);
+    for (int j = 0; j < N; ++j) {
+        mu[j] = (float)P.mu[0][j];
+        mu[N + j] = (float)P.mu[1][j];
+    }
+    if (cudaMemcpy(c->d_mu, mu.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice) != cudaSuccess)
+        return USR_ERR_CUDA;
+    const int n_out[3] = {nx, ny, nz};
+    const int Ks[3] = {nx, ny, N * nz};
+    const int lines[3] = {ny * nz, nx * nz, ny * nx};
+    const int batches[3] = {N, N, 1};
+    const long long a_rows[3] = {(long long)ny * nz, (long long)N * nx * nz, (long long)ny * nx};
+    void* a_hi[3] = {c->d_rho_hi, c->d_X_hi, c->d_Y_hi};
+    void* a_lo[3] = {c->d_rho_lo, c->d_X_lo, c->d_Y_lo};
+    void* o_hi[3] = {c->d_X_hi, c->d_Y_hi, c->d_psi};
+    void* o_lo[3] = {c->d_X_lo, c->d_Y_lo, nullptr};
+    for (int p = 0; p < 3; ++p) {
+        usr::ConvTcArgs& a = c->targs[p];
+        std::memset(&a, 0, sizeof(a));
+        tc_shape(a, n_out[p], Ks[p], bf);
+        a.pass = p + 1;
+        a.lines = lines[p];
+        a.a_rows_per_batch = p == 1 ? nx * nz : 0;
+        a.nterms = N;
+        a.nx = nx;
+        a.ny = ny;
+        a.nz = nz;
+        a.mu = p == 0 ? c->d_mu : (p == 1 ? c->d_mu + N : nullptr);
+        a.out_hi = o_hi[p];
+        a.out_lo = o_lo[p];
+        a.status = c->d_status;
+        c->tbatches[p] = batches[p];
+        std::vector<double> B = tc_table(P, p + 1, a, batches[p]);
+        if ((s = alloc(&c->d_Bt_hi[p], es * B.size())) || (s = alloc(&c->d_Bt_lo[p], es * B.size())) ||
+            (s = upload_split(B, bf, c->d_Bt_hi[p], c->d_Bt_lo[p])))
+            return s;
+        const long long b_rows = (long long)batches[p] * a.ntiles * a.NT;
+        if ((s = usr::make_tmap(&c->maps[p].a_hi, a_hi[p], bf, a_rows[p], a.K, 128)) ||
+            (s = usr::make_tmap(&c->maps[p].a_lo, a_lo[p], bf, a_rows[p], a.K, 128)) ||
+            (s = usr::make_tmap(&c->maps[p].b_hi, c->d_Bt_hi[p], bf, b_rows, a.K, a.NT)) ||
+            (s = usr::make_tmap(&c->maps[p].b_lo, c->d_Bt_lo[p], bf, b_rows, a.K, a.NT)))
+            return s;
+        // keep (CTAs per SM) x (TMEM columns) <= 512 by padding the shared memory request
+        const size_t floor_smem = (size_t)228 * 1024 * a.tmem_cols / 512 + 1024;
+        a.smem = (int)std::max(usr::conv_tc_smem(a), floor_smem);
+        if ((s = usr::conv_tc_setup(bf, (size_t)a.smem)) != USR_OK) return s;
+    }
     return USR_OK;
 }
 
@@ -146,10 +349,13 @@ void fill_args(usr_ctx* c)
     std::memset(&g, 0, sizeof(g));
     g.box = c->boxf;
     for (int ax = 0; ax < 3; ++ax) {
-        g.hh[ax] = (float)(P.h[ax] * P.h[ax] / (2.0 * P.sigma_s * P.sigma_s));
-        g.dfac[ax] = (float)(P.h[ax] / (P.sigma_s * P.sigma_s));
+        g.hh[ax] = (float)(P.h[ax] * P.h[ax] / (2.0 * P.sigma_sa[ax] * P.sigma_sa[ax]));
+        g.dfac[ax] = (float)(P.h[ax] / (P.sigma_sa[ax] * P.sigma_sa[ax]));
     }
     g.F0 = (float)P.F0;
+    g.F0d = P.F0;
+    g.wsum = (float)P.wsum;
+    g.tg = P.tile;
 }
 
 usr_status check_device(const usr_ctx* c)
@@ -190,11 +396,21 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
                      c->d_pstart, c->near, c->d_near, st);
     mark(2);
-    usr::launch_spread(P.P, P.vec_spread, c->d_spos, c->d_cell_start, c->grid, P.tile, c->d_rho,
-                       c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
+    if (c->tc)
+        usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
+                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
+    else
+        usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
+                           c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
     mark(3);
     const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const long long G = c->G;
+    if (c->tc) {
+        for (int p = 0; p < 3; ++p) {
+            usr::launch_conv_tc(c->tc_bf16, c->maps[p], c->targs[p], c->tbatches[p], st);
+            mark(4 + p);
+        }
+    } else {
     {   // x pass: all terms
         usr::ConvGemm g{};
         g.M = ny * nz; g.N = N * nx; g.K = nx;
@@ -202,7 +418,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         g.B = c->d_Bx; g.ldb = (long long)N * nx;
         g.C = c->d_X; g.ldc = nx;
         g.nb2 = 1; g.nsplit = nx; g.c_split = G;
-        g.mode = 1; g.dcw = c->d_wx; g.mean = c->d_mean;
+        g.mode = 1; g.dcw = c->d_wx; g.mean = nullptr;   // rho has its mean removed already
         usr::launch_conv(g, 1, st);
     }
     mark(4);
@@ -228,7 +444,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         usr::launch_conv(g, 1, st);
     }
     mark(6);
-    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, P.tile, out,
+    }
+    usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, st);
+    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, out,
                        c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
                        c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
     mark(7);
@@ -301,25 +519,37 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     ALLOC(c->d_mean, 1);
     ALLOC(c->d_gather_partial, (size_t)ngb * 4);
     ALLOC(c->d_energy, 4);
-    ALLOC(c->d_counters, 2);
+    ALLOC(c->d_counters, 3);
+    ALLOC(c->d_psi_partial, (size_t)usr::kGridMeanBlocks);
+    ALLOC(c->d_psi_mean, 1);
     ALLOC(c->d_in, na);
     ALLOC(c->d_out, na);
     ALLOC(c->d_near_dbg, na);
     ALLOC(c->d_far_dbg, na);
+    ALLOC(c->d_tilebuf, (size_t)nsb * usr::tile_floats(P.tile));
+    for (int a = 0; a < 3; ++a) ALLOC(c->d_tab[a], tab_ints(P, a));
 #undef ALLOC
-    if (cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
+    c->grid.psi_mean = c->d_psi_mean;
+    if (cudaMemset(c->d_counters, 0, 3 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess) {
         free_all(c);
         delete c;
         return USR_ERR_CUDA;
     }
-    if ((s = usr::grid_kernel_setup(P.P, usr::tile_bytes(P.tile))) != USR_OK) {
+    if ((s = usr::grid_kernel_setup(P.P, P.tile)) != USR_OK) {
         free_all(c);
         delete c;
         return s;
     }
     if ((s = upload_tables(c)) != USR_OK) {
+        free_all(c);
+        delete c;
+        return s;
+    }
+    c->tc = p->conv == USR_CONV_TF32X3 || p->conv == USR_CONV_BF16X3;
+    c->tc_bf16 = p->conv == USR_CONV_BF16X3;
+    if (c->tc && (s = setup_tc(c)) != USR_OK) {
         free_all(c);
         delete c;
         return s;
@@ -388,6 +618,7 @@ extern "C" usr_status usr_last_device_status(usr_ctx* c)
     if (cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return USR_ERR_CUDA;
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return USR_ERR_CUDA;
     if (v & 1) return USR_ERR_NONFINITE;
+    if (v & 4) return USR_ERR_TIMEOUT;
     return (v & 2) ? USR_ERR_INTERNAL : USR_OK;
 }
 

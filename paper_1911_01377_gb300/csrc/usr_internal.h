@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/usr.h"
@@ -18,13 +19,28 @@ constexpr int kMaxPolyDeg = 24;
 constexpr int kMaxExplicit = 8;
 constexpr int kMaxTerms = 16;
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
+constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 
-/* Cell blocks of the spreading / interpolation kernels and their smem tiles. */
+/*
+ * Cell blocks of the spreading / interpolation kernels and their smem tiles.
+ * Block b along axis a covers cells [b kb_a, min((b+1) kb_a, nc_a)); its tile
+ * spans grid points org_a[b] .. org_a[b] + T_a - 1 (periodic).  The reduction
+ * table lists, for every grid index g of axis a, the (block, tile offset)
+ * pairs whose tile holds g: red_cnt_a[g] entries at red_pair_a[g * rmax_a].
+ */
+constexpr int kTileMaxSmem = 112 * 1024;   // bytes per tile: two CTAs per SM
 struct TileGeom {
     int kb[3];      // cells per block per axis
     int nbk[3];     // blocks per axis
     int T[3];       // tile extent per axis (grid points); T[0] % 4 == 0
-    float wg[3];    // cell width in grid points, n / nc
+    int rmax[3];    // reduction-table row length per axis
+};
+
+/* Device copies of the per-axis tile tables (owned by the context). */
+struct TileTabs {
+    const int* org[3];
+    const int* red_cnt[3];
+    const int2* red_pair[3];
 };
 
 /* Host plan: everything usr_init derives from usr_params, in FP64. */
@@ -35,7 +51,9 @@ struct Plan {
     int n[3];
     double h[3];
     double sigma, c, F0;
-    double sigma_s;
+    double sigma_s;                      // largest spreading width (reported)
+    double sigma_sa[3];                  // spreading width per axis
+    double wsum;                         // sum of the spreading weights over a stencil
     int P;                               // stencil points per axis
     int N;                               // far-grid Gaussians
     std::vector<double> a, s;            // full real-space term table (a_j, s_j)
@@ -52,7 +70,9 @@ struct Plan {
     double scale[kMaxTerms];
     int cells[3];
     TileGeom tile;
-    bool vec_spread;                     // grid x extent divisible by 4: float4 reductions
+    std::vector<int> tile_org[3];        // per axis: tile origin of each block
+    std::vector<int> red_cnt[3];         // per axis: covering tiles of each grid index
+    std::vector<int> red_pair[3];        // per axis: (block, offset) pairs, rmax per grid index
 };
 
 /* Build the plan (host only).  Returns USR_OK or an error. */
@@ -82,7 +102,12 @@ struct GridArgs {
     BoxF box;
     float hh[3];          // h^2 / (2 sigma_s^2): exponent factor per stencil step
     float dfac[3];        // h / sigma_s^2: derivative factor
-    float F0;             // self-interaction constant
+    float F0;             // self-interaction constant (per-atom potential)
+    float wsum;           // sum of the spreading weights over a stencil
+    const double* psi_mean;   // grid mean of psi (its k = 0 mode, zero up to rounding)
+    double F0d;           // the same in FP64 (self energy)
+    TileGeom tg;
+    TileTabs tab;
 };
 
 struct ConvGemm {
@@ -97,6 +122,31 @@ struct ConvGemm {
     const double* mean;                          // mode 1: subtract K*mean from the row sums (may be null)
 };
 
+/* One pass of the tensor-core convolutions (k_conv_tc.cu). */
+constexpr int kConvTcMaxStages = 6;
+struct ConvTcArgs {
+    int pass;               // 1 = x, 2 = y, 3 = z
+    int lines;              // valid A rows (output lines) per batch
+    int a_rows_per_batch;   // A row offset between batches (0: all batches share A)
+    int K;                  // contraction length
+    int NT;                 // N tile (B rows per tile, multiple of 16, <= 256)
+    int cols;               // output columns per tile (the DC column follows them)
+    int ntiles;             // N tiles
+    int n_out;              // output columns in all
+    int nterms, nx, ny, nz;
+    int stages;             // TMA ring depth
+    int tmem_cols;          // tensor-memory columns allocated (power of two >= NT)
+    int smem;               // dynamic shared memory per CTA (bytes; padded so that the CTAs an SM
+                            // can hold never ask for more than 512 TMEM columns together)
+    const float* mu;        // per-term mean of the 1D kernel (passes 1, 2)
+    void* out_hi;           // pass output (hi part; FP32 psi for pass 3)
+    void* out_lo;           // pass output (lo part; unused for pass 3)
+    int* status;
+};
+struct ConvTcMaps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
 // ---- launchers (all enqueue on `st`) ----
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                 float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
@@ -108,15 +158,22 @@ void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx,
 void launch_pairs(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
                   const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, int* count,
                   unsigned long long* hash, cudaStream_t st);
-void launch_spread(int P, bool vec, const float4* spos, const int* cell_start, const GridArgs& g, const TileGeom& tg,
-                   float* rho, double* partial, unsigned int* counter, double* mean, int* status, cudaStream_t st);
+void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
+                   void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
+                   cudaStream_t st);
 void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
+usr_status make_tmap(CUtensorMap* m, const void* ptr, bool bf16, long long rows, int K, int box_rows);
+size_t conv_tc_smem(const ConvTcArgs& g);
+usr_status conv_tc_setup(bool bf16, size_t smem);
+void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int batches, cudaStream_t st);
+void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
+                      cudaStream_t st);
 void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const float4* near_out,
-                   const float* psi, const GridArgs& g, const TileGeom& tg, float4* out, float4* near_dbg,
+                   const float* psi, const GridArgs& g, float4* out, float4* near_dbg,
                    float4* far_dbg, double* partial, unsigned int* counter, double* energy, int* status,
                    cudaStream_t st);
 int tile_blocks(const TileGeom& tg);
-size_t tile_bytes(const TileGeom& tg);
-usr_status grid_kernel_setup(int P, size_t bytes);
+size_t tile_floats(const TileGeom& tg);
+usr_status grid_kernel_setup(int P, const TileGeom& tg);
 
 }  // namespace usr

@@ -175,7 +175,12 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     if (!(se.b > 1.0) || !(se.r0 > 0.0) || !(se.w0 > 0.0) || !(se.s0 > 0.0) || se.n_terms < 0 ||
         se.n_terms > kMaxTerms || se.trunc_eps < 0.0 || !std::isfinite(se.b) || !std::isfinite(se.r0))
         return USR_ERR_ARG;
-    if (p.conv != USR_CONV_FP32) return USR_ERR_ARG;
+    if (p.conv != USR_CONV_FP32 && p.conv != USR_CONV_TF32X3 && p.conv != USR_CONV_BF16X3) return USR_ERR_ARG;
+    if (p.conv != USR_CONV_FP32) {
+        const int q = p.conv == USR_CONV_BF16X3 ? 8 : 4;    // 16-byte rows for the tensor maps
+        for (int a = 0; a < 3; ++a)
+            if (p.grid[a] % q != 0) return USR_ERR_BOX;
+    }
     if (p.max_atoms < 0) return USR_ERR_ARG;
     int Pst = p.spread_points ? p.spread_points : 12;
     if (Pst < 8 || Pst > 16 || (Pst & 1)) return USR_ERR_ARG;
@@ -215,19 +220,28 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             if (trunc_bound(N, se.b, P.sigma, Lmax) <= eps) { P.N = N; break; }
         if (P.N == 0) return USR_ERR_BOX;
     }
-    // spreading Gaussian and per-term deconvolved widths
-    double hmax = std::max(P.h[0], std::max(P.h[1], P.h[2]));
-    P.sigma_s = ratio * hmax;
+    // spreading Gaussians (width ratio * h per axis, so that every axis has the
+    // same stencil reach in widths and the same aliasing) and the per-term,
+    // per-axis deconvolved widths sqrt(s_j^2 - 2 sigma_a^2) of Eq. 32.  Per axis,
+    // exp(-x^2 / (2 s^2)) = (s / w) (2 pi sigma^2)^-1 (e_sigma * e_w * e_sigma)(x)
+    // with e_v(x) = exp(-x^2 / (2 v^2)); the two spreading legs become grid sums
+    // (a factor h each).
     double dV = P.h[0] * P.h[1] * P.h[2];
-    double norm_s = std::pow(2.0 * kPi * P.sigma_s * P.sigma_s, -3.0);   // two spreading Gaussians
+    for (int a = 0; a < 3; ++a) P.sigma_sa[a] = ratio * P.h[a];
+    P.sigma_s = std::max(P.sigma_sa[0], std::max(P.sigma_sa[1], P.sigma_sa[2]));
     for (int j = 0; j < P.N; ++j) {
-        double wc2 = P.s[j] * P.s[j] - 2.0 * P.sigma_s * P.sigma_s;
-        if (!(wc2 > 0.0)) return USR_ERR_BOX;
-        double wc = std::sqrt(wc2);
-        double Aj = P.a[j] * std::pow(P.s[j] / wc, 3.0);
-        P.scale[j] = Aj * dV * dV * norm_s;
-        for (int a = 0; a < 3; ++a) P.mu[a][j] = periodic_kernel(wc, P.h[a], P.n[a], P.ktil[a][j]);
+        double f = P.a[j] * dV * dV;
+        for (int a = 0; a < 3; ++a) {
+            double wc2 = P.s[j] * P.s[j] - 2.0 * P.sigma_sa[a] * P.sigma_sa[a];
+            if (!(wc2 > 0.0)) return USR_ERR_BOX;
+            double wc = std::sqrt(wc2);
+            f *= (P.s[j] / wc) / (2.0 * kPi * P.sigma_sa[a] * P.sigma_sa[a]);
+            P.mu[a][j] = periodic_kernel(wc, P.h[a], P.n[a], P.ktil[a][j]);
+        }
+        P.scale[j] = f;
     }
+    // sum of the spreading weights over a stencil: prod_a sqrt(2 pi) sigma_a / h_a
+    P.wsum = std::pow(2.0 * kPi, 1.5) * ratio * ratio * ratio;
     // pair kernel form of F: explicit narrow Gaussians + polynomial in u = r^2
     double rc2 = p.r_c * p.r_c;
     P.n_explicit = 0;
@@ -241,14 +255,17 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             ++P.n_explicit;
         }
     }
-    // cell blocks of the spreading / interpolation kernels: cores of about 13
-    // grid points, at least 256 blocks when the cell list allows, tiles <= 100 KB
+    // cell blocks of the spreading / interpolation kernels: cores of about 16
+    // grid points (the tiles' halo of P + 3 points makes small cores costly),
+    // tiles within kTileMaxSmem, at least 128 blocks when the cell list allows,
+    // at most 64 (z, y) cell rows per block
     {
         TileGeom& tg = P.tile;
+        double wg[3];
+        for (int a = 0; a < 3; ++a) wg[a] = (double)P.n[a] / P.cells[a];
         auto extent = [&](int a, int kb) {
-            const double wg = (double)P.n[a] / P.cells[a];
-            int T = (int)std::ceil(kb * wg - 1e-9) + P.P + 3;
-            if (a == 0) T = ((T + 3 + 3) / 4) * 4;
+            int T = (int)std::ceil(kb * wg[a] - 1e-9) + P.P + 3;
+            if (a == 0) T = ((T + 3) / 4) * 4;
             return T;
         };
         auto nblocks = [&]() {
@@ -257,10 +274,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             return nb;
         };
         auto bytes = [&]() { return 4.0 * extent(0, tg.kb[0]) * extent(1, tg.kb[1]) * extent(2, tg.kb[2]); };
-        for (int a = 0; a < 3; ++a) {
-            const double wg = (double)P.n[a] / P.cells[a];
-            tg.kb[a] = std::max(1, std::min(P.cells[a], (int)std::floor(13.0 / wg)));
-        }
+        for (int a = 0; a < 3; ++a) tg.kb[a] = std::max(1, std::min(P.cells[a], (int)std::floor(16.0 / wg[a])));
         auto shrink = [&]() {
             int best = -1;
             for (int a = 2; a >= 0; --a)
@@ -269,15 +283,34 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             --tg.kb[best];
             return true;
         };
-        while (nblocks() < 256 && shrink()) {}
-        while (bytes() > 100.0 * 1024 && shrink()) {}
-        if (bytes() > 200.0 * 1024) return USR_ERR_BOX;
+        while ((bytes() > kTileMaxSmem || tg.kb[1] * tg.kb[2] > 64) && shrink()) {}
+        while (nblocks() < 128 && shrink()) {}
+        if (bytes() > kTileMaxSmem) return USR_ERR_BOX;
         for (int a = 0; a < 3; ++a) {
             tg.nbk[a] = (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
             tg.T[a] = extent(a, tg.kb[a]);
-            tg.wg[a] = (float)((double)P.n[a] / P.cells[a]);
+            const int H = P.P / 2;
+            P.tile_org[a].resize(tg.nbk[a]);
+            std::vector<std::vector<int>> lists(P.n[a]);
+            for (int b = 0; b < tg.nbk[a]; ++b) {
+                const int o = (int)std::floor(b * tg.kb[a] * wg[a] + 1e-9) - H - 1;
+                P.tile_org[a][b] = o;
+                for (int t = 0; t < tg.T[a]; ++t) {
+                    const int gi = (((o + t) % P.n[a]) + P.n[a]) % P.n[a];
+                    lists[gi].push_back(b);
+                    lists[gi].push_back(t);
+                }
+            }
+            int rmax = 0;
+            for (auto& l : lists) rmax = std::max(rmax, (int)l.size() / 2);
+            tg.rmax[a] = rmax;
+            P.red_cnt[a].assign(P.n[a], 0);
+            P.red_pair[a].assign((size_t)P.n[a] * rmax * 2, 0);
+            for (int gi = 0; gi < P.n[a]; ++gi) {
+                P.red_cnt[a][gi] = (int)lists[gi].size() / 2;
+                std::copy(lists[gi].begin(), lists[gi].end(), P.red_pair[a].begin() + (size_t)gi * rmax * 2);
+            }
         }
-        P.vec_spread = (P.n[0] % 4) == 0;
     }
     static const int kDegs[] = {8, 10, 12, 16, 20, 24};
     P.poly_deg = 0;

@@ -65,11 +65,16 @@ def test_plan_matches_closed_forms(libusr, tables, r_c):
 def test_plan_rejects_unsupported_input(libusr):
     ok = dict(box=(31.0, 31.0, 31.0), grid=(32, 32, 32), r_c=9.0, series="C1_B2")
     usr.usr_plan(usr.make_params(**ok))
+    usr.usr_plan(usr.make_params(**dict(ok, conv=1)))
+    usr.usr_plan(usr.make_params(**dict(ok, grid=(36, 32, 32), conv=1)))
+    usr.usr_plan(usr.make_params(**dict(ok, conv=2)))
     bad = [dict(ok, r_c=11.0),                    # fewer than 3 cells on an axis
            dict(ok, r_c=-1.0),
            dict(ok, grid=(32, 16, 32)),           # fewer than spread_points + 8 points
            dict(ok, box=(31.0, 0.0, 31.0)),
-           dict(ok, spread_sigma_over_h=3.5)]     # sigma_0^2 <= 2 sigma_s^2
+           dict(ok, spread_sigma_over_h=3.5),     # sigma_0^2 <= 2 sigma_s^2
+           dict(ok, grid=(30, 32, 32), conv=1),   # TF32x3 needs grid dims that are multiples of 4
+           dict(ok, grid=(36, 32, 32), conv=2)]   # BF16x3 needs multiples of 8
     for kw in bad:
         with pytest.raises(usr.UsrError) as e:
             usr.usr_plan(usr.make_params(**kw))
