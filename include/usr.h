@@ -114,6 +114,8 @@ typedef struct {
     int poly_degree;       /* degree of the FP32 polynomial for the wide terms of F */
     int n_explicit;        /* leading Gaussians of F evaluated explicitly in the pair kernel */
     double poly_max_err;   /* max |error| of that polynomial on [0, r_c], relative to F(0) */
+    double device_bytes;   /* usr_plan: device memory a new context for these parameters needs;
+                              usr_info: device memory the context holds (its buffers only grow) */
 } usr_plan_info;
 
 /* Fill *out with a preset row (n_terms = 0, trunc_eps = 0).  Host only. */
@@ -141,6 +143,20 @@ typedef struct usr_ctx usr_ctx;
  */
 usr_status usr_init(const usr_params* p, usr_ctx** out);
 
+/*
+ * Point an existing context at another system (box, grid, cutoff, series,
+ * spreading, convolution form, max_atoms): the plan is rebuilt on the host,
+ * device buffers that are already large enough are reused, and the tables are
+ * uploaded with asynchronous copies on `stream` (so evaluations enqueued after
+ * it on the same stream see them).  Buffers too small for the new system are
+ * reallocated, which synchronises the device; among systems no larger than
+ * one the context has held before, nothing is allocated.  The paper has no
+ * counterpart: this serves many independent systems from a pool of contexts.
+ * Errors as usr_plan / usr_init; on error the context must be reconfigured
+ * successfully or destroyed before further use.
+ */
+usr_status usr_reconfigure(usr_ctx* ctx, const usr_params* p, void* stream);
+
 /* Free a context and its device memory (NULL is ignored).  Synchronises. */
 void usr_destroy(usr_ctx* ctx);
 
@@ -166,11 +182,71 @@ usr_status usr_eval(usr_ctx* ctx, int n, const float* xyzq, float* out, double* 
 usr_status usr_eval_host(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
 
 /*
+ * usr_eval_host without the final synchronisation: the copies and the
+ * evaluation are enqueued on `stream` and the call returns at once.  xyzq,
+ * out and energy (host, 4 doubles, may be NULL) must stay valid and unread
+ * until the stream reaches this point (record an event after the call);
+ * pinned host memory makes the copies asynchronous.
+ */
+usr_status usr_eval_host_async(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
+
+/*
  * Synchronise the context's last stream and return the device status of the
  * evaluations since the previous call (USR_OK, USR_ERR_NONFINITE or
  * USR_ERR_INTERNAL), then clear it.
  */
 usr_status usr_last_device_status(usr_ctx* ctx);
+
+/* ---- serving: continuous batching of independent systems ------------- */
+
+/*
+ * A server evaluates a stream of independent systems (each its own box, grid,
+ * cutoff and charges) on the current device.  Requests are queued by
+ * usr_server_submit from any host thread; a worker thread admits them in
+ * arrival order onto `slots` concurrent evaluation slots, each a context with
+ * its own CUDA stream, as soon as a slot is free and the device memory all
+ * slots hold stays within hbm_budget_bytes.  Requests that arrive while
+ * others run are admitted as slots and memory free up, and their work
+ * overlaps on the device.  A slot's context is re-targeted to each request
+ * with usr_reconfigure, so cell lists, grids and tables stay resident and are
+ * reused; memory is allocated only when a request is larger than anything
+ * its slot held before.  The paper has no counterpart: it describes the
+ * method for one system.
+ */
+typedef struct usr_server usr_server;
+typedef struct {
+    double hbm_budget_bytes;   /* device memory all slots may hold; 0 = 16 GiB */
+    int slots;                 /* evaluations in flight at once (1..64); 0 = 8 */
+} usr_server_params;
+
+usr_status usr_server_create(const usr_server_params* p, usr_server** out);
+
+/*
+ * Queue one evaluation: p describes the system (p->max_atoms >= n), xyzq is
+ * host memory (n rows x, y, z, q), out (n rows Fx, Fy, Fz, phi) and energy
+ * (4 doubles, may be NULL) host memory the server writes.  All three must
+ * stay valid until the request completes; pinned memory lets the copies
+ * overlap.  *ticket identifies the request.  Thread-safe.
+ */
+usr_status usr_server_submit(usr_server* s, const usr_params* p, int n, const float* xyzq, float* out,
+                             double* energy, long long* ticket);
+
+/*
+ * Move up to max completed requests out of the server: their tickets, the
+ * latency from submission to results in host memory (ms) and their status
+ * (USR_OK, or why the request failed: USR_ERR_OOM if it can never fit the
+ * budget, a plan error, a device status).  Returns the number written.
+ */
+int usr_server_poll(usr_server* s, long long* tickets, double* latency_ms, int* status, int max);
+
+/* Block until every submitted request has completed (timeout_s <= 0: no limit). */
+usr_status usr_server_wait(usr_server* s, double timeout_s);
+
+/* Device bytes the slots hold, requests waiting for admission, requests on the device. */
+usr_status usr_server_info(usr_server* s, double* held_bytes, long long* queued, long long* in_flight);
+
+/* Finish the queued requests, then free every slot (NULL is ignored). */
+void usr_server_destroy(usr_server* s);
 
 /* Static description of a status code. */
 const char* usr_status_string(usr_status s);

@@ -9,9 +9,9 @@
  *            folded into the convolution scale).  The CTA's warps own disjoint
  *            sets of tile rows (y = warp mod 8) and every warp walks the
  *            block's atoms in sorted order, adding the stencil columns of its
- *            rows (one lane per column, all P planes) with plain shared-memory
- *            read-modify-writes: no atomics, and every tile point receives its
- *            terms in a fixed order.  The
+ *            rows (one lane per column and group of planes) with plain
+ *            shared-memory read-modify-writes: no atomics, and every tile point
+ *            receives its terms in a fixed order.  The
  *            tile is stored whole to a tile buffer, and the block's tile sum
  *            is kept; the last CTA forms the grid mean (the k = 0 mode,
  *            dropped per Eq. 4) from those sums in block order.
@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 64;          // atoms whose weights are staged at once (spread)
+constexpr int kChunk = 128;         // atoms whose weights are staged at once (spread)
 constexpr int kGChunk = 128;        // atoms staged at once (gather)
 constexpr int kMaxRows = 64;        // (cz, cy) rows of cells per block
 
@@ -127,12 +127,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
                                                         double* __restrict__ mean, int* __restrict__ status)
 {
     constexpr int H = P / 2;
-    static_assert(2 * P <= 32 && P <= 2 * kWarps, "two stencil rows per warp, one lane per (row, column)");
+    static_assert(P <= 2 * kWarps && P <= 32, "at most two stencil rows per warp");
     extern __shared__ float4 smem4[];
     float* tile = reinterpret_cast<float*>(smem4);
     constexpr int PA = (P + 3) & ~3;              // weight rows padded to 16 bytes
     __shared__ __align__(16) float W[kChunk][3][PA];
     __shared__ int B[kChunk][3];
+    __shared__ float4 sp[kChunk];
     __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
     __shared__ double red[kWarps];
     __shared__ int is_last;
@@ -150,11 +151,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
 
     for (int c0 = 0; c0 < natoms; c0 += kChunk) {
         const int nch = min(kChunk, natoms - c0);
-        // phase 1: per-atom 1D weights (q folded into the x weights) and tile base
+        // phase 1: stage the chunk's positions, then per-atom 1D weights (q folded
+        // into the x weights) and tile base
+        for (int a = threadIdx.x; a < nch; a += kThreads) sp[a] = pos[block_atom(c0 + a, rs, pre)];
+        __syncthreads();
         for (int idx = threadIdx.x; idx < nch * 3 * P; idx += kThreads) {
             const int a = idx / (3 * P), rem = idx - a * 3 * P;
             const int ax = rem / P, k = rem - ax * P;
-            const float4 p = pos[block_atom(c0 + a, rs, pre)];
+            const float4 p = sp[a];
             // per-axis constants selected without dynamic indexing (keeps them in registers)
             const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
             const float gs = ax == 0 ? g.box.gs[0] : (ax == 1 ? g.box.gs[1] : g.box.gs[2]);
@@ -177,25 +181,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
         }
         __syncthreads();
         // phase 2: warp w owns the tile rows ty = w (mod 8); for each atom it adds
-        // the stencil columns of its rows, all P planes of a column per lane
-        for (int a = 0; a < nch; ++a) {
-            const int bx = B[a][0], by = B[a][1], bz = B[a][2];
-            if (bx < 0 || by < 0 || bz < 0) continue;
-            const int jy = ((warp - by) % kWarps + kWarps) % kWarps + kWarps * (lane / P);
-            const int jx = lane % P;
-            if (lane >= 2 * P || jy >= P) continue;
-            const float v = W[a][0][jx] * W[a][1][jy];
-            float* col = tile + ((bz * Ty + by + jy) * Tx + bx + jx);
-            float wz[PA], t[P];
-            #pragma unroll
-            for (int k = 0; k < PA; k += 4) {
-                const float4 w4 = *reinterpret_cast<const float4*>(&W[a][2][k]);
-                wz[k] = w4.x; wz[k + 1] = w4.y; wz[k + 2] = w4.z; wz[k + 3] = w4.w;
+        // the stencil columns of its one or two rows.  Lane = (column jx, group of
+        // planes): P columns x G groups, each lane updating PG consecutive planes.
+        {
+            constexpr int G = 32 / P;                  // plane groups per row
+            constexpr int PG = (P + G - 1) / G;        // planes per lane
+            const int jx = lane % P, grp = lane / P;
+            const int k0 = grp * PG;
+            for (int a = 0; a < nch; ++a) {
+                const int bx = B[a][0], by = B[a][1], bz = B[a][2];
+                if (bx < 0 || by < 0 || bz < 0 || grp >= G) continue;
+                float wz[PG];
+                #pragma unroll
+                for (int k = 0; k < PG; ++k) wz[k] = (k0 + k < P) ? W[a][2][k0 + k] : 0.f;
+                const float wxa = W[a][0][jx];
+                for (int jy = ((warp - by) % kWarps + kWarps) % kWarps; jy < P; jy += kWarps) {
+                    const float v = wxa * W[a][1][jy];
+                    float* col = tile + (((bz + k0) * Ty + by + jy) * Tx + bx + jx);
+                    float t[PG];
+                    #pragma unroll
+                    for (int k = 0; k < PG; ++k)
+                        if (k0 + k < P) t[k] = col[k * TXY];
+                    #pragma unroll
+                    for (int k = 0; k < PG; ++k)
+                        if (k0 + k < P) col[k * TXY] = fmaf(v, wz[k], t[k]);
+                }
             }
-            #pragma unroll
-            for (int k = 0; k < P; ++k) t[k] = col[k * TXY];
-            #pragma unroll
-            for (int k = 0; k < P; ++k) col[k * TXY] = fmaf(v, wz[k], t[k]);
         }
         __syncthreads();
     }
@@ -384,14 +395,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int col_jx[NIT], col_jy[NIT], col_off[NIT];
-    #pragma unroll
-    for (int it = 0; it < NIT; ++it) {
-        const int pp = lane + 32 * it;
-        col_jy[it] = pp < P * P ? pp / P : -1;
-        col_jx[it] = pp < P * P ? pp - (pp / P) * P : 0;
-        col_off[it] = max(col_jy[it], 0) * Tx + col_jx[it];
-    }
+    // four lanes (a quad) per atom, eight atoms per warp: lane u of a quad takes
+    // the stencil columns jx = u, u + 4, ... of every row, contracting z first
+    constexpr int NC = (P + 3) / 4;
+    const int quad = lane >> 2, u = lane & 3;
     double e_tot = 0.0, e_near = 0.0, e_far = 0.0, e_self = 0.0;
     const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
     for (int c0 = 0; c0 < natoms; c0 += kGChunk) {
@@ -404,87 +411,106 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict
             si[a] = perm[s];
         }
         __syncthreads();
-    for (int j = warp; j < nch; j += kWarps) {
-        const float4 p = sp[j];
-        const float pc[3] = {p.x, p.y, p.z};
-        int base[3];
-        float wk[3], dk[3];              // lane k < P: weight and derivative factor of stencil point k
-        bool ok = true;
-        #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float u = pc[a] * g.box.gs[a];
-            const float f = floorf(u);
-            const float t = u - f;
-            base[a] = (int)f - H + 1 - bg.o[a];
-            ok = ok && base[a] >= 0 && base[a] + P <= g.tg.T[a];
-            const float d = (float)(min(lane, P - 1) - H + 1) - t;
-            wk[a] = __expf(-d * d * g.hh[a]);
-            dk[a] = wk[a] * d * g.dfac[a];
-        }
-        float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-        if (ok) {
-            float wz[P], dz[P];
+        for (int j0 = warp * 8; j0 < nch; j0 += kWarps * 8) {
+            const int j = j0 + quad;
+            const bool have = j < nch;
+            const float4 p = sp[have ? j : j0];
+            const float pc[3] = {p.x, p.y, p.z};
+            int base[3];
+            float tt[3];
+            bool ok = have;
             #pragma unroll
-            for (int k = 0; k < P; ++k) {
-                wz[k] = __shfl_sync(0xffffffffu, wk[2], k);
-                dz[k] = __shfl_sync(0xffffffffu, dk[2], k);
+            for (int a = 0; a < 3; ++a) {
+                const float uu = pc[a] * g.box.gs[a];
+                const float f = floorf(uu);
+                tt[a] = uu - f;
+                base[a] = (int)f - H + 1 - bg.o[a];
+                ok = ok && base[a] >= 0 && base[a] + P <= g.tg.T[a];
             }
-            const float* b0 = tile + ((base[2] * Ty + base[1]) * Tx + base[0]);
-            #pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int jx = col_jx[it], jy = max(col_jy[it], 0);
-                const float wx = __shfl_sync(0xffffffffu, wk[0], jx);
-                const float dwx = __shfl_sync(0xffffffffu, dk[0], jx);
-                const float wy = __shfl_sync(0xffffffffu, wk[1], jy);
-                const float dwy = __shfl_sync(0xffffffffu, dk[1], jy);
-                if (col_jy[it] >= 0) {
-                    const float* col = b0 + col_off[it];
-                    float v[P];
-                    #pragma unroll
-                    for (int k = 0; k < P; ++k) v[k] = col[k * TXY];
-                    // two interleaved partial sums per contraction (shorter FMA chains)
-                    float c0a = 0.f, c0b = 0.f, c1a = 0.f, c1b = 0.f;
-                    #pragma unroll
-                    for (int k = 0; k < P; k += 2) {
-                        c0a = fmaf(wz[k], v[k], c0a);
-                        c1a = fmaf(dz[k], v[k], c1a);
-                        c0b = fmaf(wz[k + 1], v[k + 1], c0b);
-                        c1b = fmaf(dz[k + 1], v[k + 1], c1b);
-                    }
-                    const float cz0 = c0a + c0b, cz1 = c1a + c1b;
-                    const float wxy = wx * wy;
-                    aphi = fmaf(wxy, cz0, aphi);
-                    ax = fmaf(dwx * wy, cz0, ax);
-                    ay = fmaf(wx * dwy, cz0, ay);
-                    az = fmaf(wxy, cz1, az);
+            float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+            if (ok) {
+                float wz[P], dz[P], wy[P], dy[P], wx[NC], dx[NC];
+                #pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const float d2 = (float)(k - H + 1) - tt[2];
+                    wz[k] = __expf(-d2 * d2 * g.hh[2]);
+                    dz[k] = wz[k] * d2 * g.dfac[2];
+                    const float d1 = (float)(k - H + 1) - tt[1];
+                    wy[k] = __expf(-d1 * d1 * g.hh[1]);
+                    dy[k] = wy[k] * d1 * g.dfac[1];
                 }
+                #pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const float d0 = (float)(u + 4 * m - H + 1) - tt[0];
+                    wx[m] = (u + 4 * m < P) ? __expf(-d0 * d0 * g.hh[0]) : 0.f;
+                    dx[m] = wx[m] * d0 * g.dfac[0];
+                }
+                const float* b0 = tile + ((base[2] * Ty + base[1]) * Tx + base[0] + u);
+                #pragma unroll
+                for (int jy = 0; jy < P; ++jy) {
+                    const float* row = b0 + jy * Tx;
+                    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+                    #pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        if (u + 4 * m >= P) continue;
+                        const float* col = row + 4 * m;
+                        float v[P];
+                        #pragma unroll
+                        for (int k = 0; k < P; ++k) v[k] = col[k * TXY];
+                        float c0a = 0.f, c0b = 0.f, c1a = 0.f, c1b = 0.f;
+                        #pragma unroll
+                        for (int k = 0; k < P; k += 2) {
+                            c0a = fmaf(wz[k], v[k], c0a);
+                            c1a = fmaf(dz[k], v[k], c1a);
+                            c0b = fmaf(wz[k + 1], v[k + 1], c0b);
+                            c1b = fmaf(dz[k + 1], v[k + 1], c1b);
+                        }
+                        const float cz0 = c0a + c0b, cz1 = c1a + c1b;
+                        r0 = fmaf(wx[m], cz0, r0);
+                        r1 = fmaf(dx[m], cz0, r1);
+                        r2 = fmaf(wx[m], cz1, r2);
+                    }
+                    aphi = fmaf(wy[jy], r0, aphi);
+                    ax = fmaf(wy[jy], r1, ax);
+                    ay = fmaf(dy[jy], r0, ay);
+                    az = fmaf(wy[jy], r2, az);
+                }
+            } else if (have && u == 0) {
+                atomicOr(status, 2);          // cannot happen for wrapped positions
             }
-        } else if (lane == 0) {
-            atomicOr(status, 2);          // cannot happen for wrapped positions
-        }
-        aphi = warp_sum_f(aphi) - phi_dc;
-        ax = warp_sum_f(ax);
-        ay = warp_sum_f(ay);
-        az = warp_sum_f(az);
-        if (lane == 0) {
-            const int i = si[j];
-            const float qi = p.w;
-            const float4 nr = sn[j];
-            const float fx = -qi * ax, fy = -qi * ay, fz = -qi * az;
-            const float phi = nr.w + aphi - g.F0 * qi;
-            out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
-            if (near_dbg) near_dbg[i] = nr;
-            if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
-            const double en = 0.5 * (double)qi * (double)nr.w;
-            const double ef = 0.5 * (double)qi * (double)aphi;
-            const double es = -0.5 * g.F0d * (double)qi * (double)qi;
-            e_near += en;
-            e_far += ef;
-            e_self += es;
-            e_tot += en + ef + es;
+            // the four lanes of a quad hold disjoint partial sums
+            #pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+            }
+            aphi -= phi_dc;
+            if (have && u == 0) {
+                const int i = si[j];
+                const float qi = p.w;
+                const float4 nr = sn[j];
+                const float fx = -qi * ax, fy = -qi * ay, fz = -qi * az;
+                const float phi = nr.w + aphi - g.F0 * qi;
+                out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
+                if (near_dbg) near_dbg[i] = nr;
+                if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
+                const double en = 0.5 * (double)qi * (double)nr.w;
+                const double ef = 0.5 * (double)qi * (double)aphi;
+                const double es = -0.5 * g.F0d * (double)qi * (double)qi;
+                e_near += en;
+                e_far += ef;
+                e_self += es;
+                e_tot += en + ef + es;
+            }
         }
     }
-    }
+    // per-warp energy sums in a fixed order (lanes 0, 4, ..., 28 hold atoms)
+    e_tot = warp_sum_d(e_tot);
+    e_near = warp_sum_d(e_near);
+    e_far = warp_sum_d(e_far);
+    e_self = warp_sum_d(e_self);
     if (lane == 0) {
         red[warp][0] = e_tot;
         red[warp][1] = e_near;
@@ -539,16 +565,14 @@ static void set_smem(size_t bytes)
     cudaFuncSetAttribute(k_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-usr_status grid_kernel_setup(int P, const TileGeom& tg)
+/* Allow every stencil variant the largest tile a plan may choose. */
+usr_status grid_kernel_setup(size_t bytes)
 {
-    const size_t bytes = sizeof(float) * tile_floats(tg);
-    switch (P) {
-        case 8: set_smem<8>(bytes); break;
-        case 10: set_smem<10>(bytes); break;
-        case 12: set_smem<12>(bytes); break;
-        case 14: set_smem<14>(bytes); break;
-        default: set_smem<16>(bytes); break;
-    }
+    set_smem<8>(bytes);
+    set_smem<10>(bytes);
+    set_smem<12>(bytes);
+    set_smem<14>(bytes);
+    set_smem<16>(bytes);
     return cudaGetLastError() == cudaSuccess ? USR_OK : USR_ERR_CUDA;
 }
 

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos
                         }
                         float dFdu = dp * a.two_over_rc2;
                         for (int e = 0; e < a.n_explicit; ++e) {
-                            const float g = a.ea[e] * expf(-r2 * a.einv[e]);
+                            const float g = a.ea[e] * __expf(-r2 * a.einv[e]);
                             p += g;
                             dFdu = fmaf(-g, a.einv[e], dFdu);
                         }
@@ -154,6 +154,8 @@ void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx,
                  const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st)
 {
     switch (deg) {
+        case 6: launch_cl<6, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
+        case 7: launch_cl<7, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
         case 8: launch_cl<8, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
         case 10: launch_cl<10, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
         case 12: launch_cl<12, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;

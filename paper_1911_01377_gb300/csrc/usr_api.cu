@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 
 #include <cuda_bf16.h>
 
@@ -55,6 +56,12 @@ struct usr_ctx {
     usr::ConvTcMaps maps[3];
     usr::ConvTcArgs targs[3];
     int tbatches[3] = {0, 0, 0};
+    // allocated bytes of every device buffer (buffers only grow), and the
+    // pinned staging area of the table uploads with the event of its last use
+    std::unordered_map<void**, size_t> cap;
+    unsigned char* h_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
     // host-buffer staging and inspection
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
     bool keep_parts = false;
@@ -97,6 +104,8 @@ void free_all(usr_ctx* c)
         if (p) cudaFree(p);
     if (c->ev_made)
         for (auto& e : c->ev) cudaEventDestroy(e);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -117,49 +126,6 @@ void fill_box(const Plan& P, usr::BoxF& b)
         b.nc[a] = P.cells[a];
         b.n[a] = P.n[a];
     }
-}
-
-usr_status upload_tables(usr_ctx* c)
-{
-    const Plan& P = c->plan;
-    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    std::vector<float> Bx((size_t)nx * N * nx), Ay((size_t)N * ny * ny), Az((size_t)nz * N * nz);
-    std::vector<float> wx((size_t)N * nx), wy((size_t)N * ny), wz((size_t)N * nz);
-    for (int j = 0; j < N; ++j) {
-        for (int k = 0; k < nx; ++k)
-            for (int m = 0; m < nx; ++m)
-                Bx[(size_t)k * N * nx + j * nx + m] = (float)P.ktil[0][j][((m - k) % nx + nx) % nx];
-        for (int m = 0; m < ny; ++m)
-            for (int k = 0; k < ny; ++k)
-                Ay[((size_t)j * ny + m) * ny + k] = (float)P.ktil[1][j][((m - k) % ny + ny) % ny];
-        for (int m = 0; m < nz; ++m)
-            for (int k = 0; k < nz; ++k)
-                Az[(size_t)m * N * nz + j * nz + k] = (float)(P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz]);
-        for (int m = 0; m < nx; ++m) wx[(size_t)j * nx + m] = (float)P.mu[0][j];
-        for (int k = 0; k < ny; ++k) wy[(size_t)j * ny + k] = (float)P.mu[1][j];
-        for (int k = 0; k < nz; ++k) wz[(size_t)j * nz + k] = (float)(P.scale[j] * P.mu[2][j]);
-    }
-    struct Up { float* d; const std::vector<float>* h; } ups[] = {
-        {c->d_Bx, &Bx}, {c->d_Ay, &Ay}, {c->d_Az, &Az}, {c->d_wx, &wx}, {c->d_wy, &wy}, {c->d_wz, &wz}};
-    for (auto& u : ups)
-        if (cudaMemcpy(u.d, u.h->data(), sizeof(float) * u.h->size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return USR_ERR_CUDA;
-    // per axis: tile origins, then reduction counts, then (block, offset) pairs
-    for (int a = 0; a < 3; ++a) {
-        std::vector<int> t;
-        t.insert(t.end(), P.tile_org[a].begin(), P.tile_org[a].end());
-        t.insert(t.end(), P.red_cnt[a].begin(), P.red_cnt[a].end());
-        while (t.size() % 2) t.push_back(0);
-        t.insert(t.end(), P.red_pair[a].begin(), P.red_pair[a].end());
-        if (cudaMemcpy(c->d_tab[a], t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return USR_ERR_CUDA;
-        const size_t off_cnt = P.tile_org[a].size();
-        const size_t off_pair = (off_cnt + P.red_cnt[a].size() + 1) / 2 * 2;
-        c->grid.tab.org[a] = c->d_tab[a];
-        c->grid.tab.red_cnt[a] = c->d_tab[a] + off_cnt;
-        c->grid.tab.red_pair[a] = reinterpret_cast<const int2*>(c->d_tab[a] + off_pair);
-    }
-    return USR_OK;
 }
 
 size_t tab_ints(const Plan& P, int a)
@@ -194,32 +160,9 @@ void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16)
     int S = (int)((200 * 1024) / stage);
     S = std::min(S, std::min(nk, 4));
     a.stages = std::max(1, std::min(S, usr::kConvTcMaxStages));
-}
-
-/* Split a table of doubles into hi/lo device arrays of the pass element type. */
-usr_status upload_split(const std::vector<double>& v, bool bf16, void* hi, void* lo)
-{
-    const size_t n = v.size();
-    if (bf16) {
-        std::vector<__nv_bfloat16> h(n), l(n);
-        for (size_t i = 0; i < n; ++i) {
-            h[i] = __float2bfloat16_rn((float)v[i]);
-            l[i] = __float2bfloat16_rn((float)(v[i] - (double)__bfloat162float(h[i])));
-        }
-        if (cudaMemcpy(hi, h.data(), 2 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(lo, l.data(), 2 * n, cudaMemcpyHostToDevice) != cudaSuccess)
-            return USR_ERR_CUDA;
-    } else {
-        std::vector<float> h(n), l(n);
-        for (size_t i = 0; i < n; ++i) {
-            h[i] = tf32_rna((float)v[i]);
-            l[i] = tf32_rna((float)(v[i] - (double)h[i]));
-        }
-        if (cudaMemcpy(hi, h.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(lo, l.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess)
-            return USR_ERR_CUDA;
-    }
-    return USR_OK;
+    // keep (CTAs per SM) x (TMEM columns) <= 512 by padding the shared memory request
+    const size_t floor_smem = (size_t)228 * 1024 * a.tmem_cols / 512 + 1024;
+    a.smem = (int)std::max(usr::conv_tc_smem(a), floor_smem);
 }
 
 /*
@@ -258,75 +201,282 @@ std::vector<double> tc_table(const Plan& P, int pass, const usr::ConvTcArgs& a, 
     return B;
 }
 
-usr_status setup_tc(usr_ctx* c)
+/* Grow a device buffer to at least `bytes` (contents are not kept; growing synchronises). */
+usr_status ensure(usr_ctx* c, void** p, size_t bytes)
 {
-    const Plan& P = c->plan;
-    const bool bf = c->tc_bf16;
-    const size_t es = bf ? 2 : 4;
-    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const size_t G = (size_t)c->G;
-    auto alloc = [&](void** p, size_t bytes) {
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            *p = nullptr;
-            return e == cudaErrorMemoryAllocation ? USR_ERR_OOM : USR_ERR_CUDA;
+    if (bytes == 0) bytes = 16;
+    auto it = c->cap.find(p);
+    if (it != c->cap.end() && it->second >= bytes && *p) return USR_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        c->cap[p] = 0;
+        return e == cudaErrorMemoryAllocation ? USR_ERR_OOM : USR_ERR_CUDA;
+    }
+    c->cap[p] = bytes;
+    return USR_OK;
+}
+
+/* Host tables of one configuration, packed for one staged upload. */
+struct Staged {
+    std::vector<unsigned char> bytes;
+    struct Item { void* dst; size_t off, len; };
+    std::vector<Item> items;
+    template <typename T>
+    void add(void* dst, const T* src, size_t count)
+    {
+        size_t off = (bytes.size() + 255) / 256 * 256;
+        bytes.resize(off + sizeof(T) * count);
+        std::memcpy(bytes.data() + off, src, sizeof(T) * count);
+        items.push_back({dst, off, sizeof(T) * count});
+    }
+};
+
+void fill_args(usr_ctx* c);
+
+}  // namespace
+
+/* Mirrors the buffer list of configure (sizes in bytes, each at least 16). */
+double usr::plan_device_bytes(const Plan& P)
+{
+    const bool tc = P.p.conv == USR_CONV_TF32X3 || P.p.conv == USR_CONV_BF16X3;
+    const double na = P.p.max_atoms > 0 ? P.p.max_atoms : 1;
+    const double ncell = (double)P.cells[0] * P.cells[1] * P.cells[2];
+    const double G = (double)P.n[0] * P.n[1] * P.n[2], N = P.N;
+    const double nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const double nsb = tile_blocks(P.tile);
+    const double ncl = std::floor((na + 7 * ncell + 7) / 8);
+    double b = 4 * ncell * 3 + 16 * ncl * 8 + 4 * ncl * 8 + 4 * ncl + 32 * ncl;   // cells, clusters
+    b += na * (4 * 4 + 16 * 7);                                                    // per-atom arrays
+    b += 4 * G + 8 * nsb * 5 + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
+    for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
+    if (!tc) {
+        b += 4 * G * (1 + 2 * N) + 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz);
+    } else {
+        const double es = P.p.conv == USR_CONV_BF16X3 ? 2 : 4;
+        b += es * G * 2 * (1 + 2 * N) + 8 * N;
+        const double n_out[3] = {nx, ny, nz}, K[3] = {nx, ny, N * nz}, bat[3] = {N, N, 1};
+        for (int p = 0; p < 3; ++p) {
+            const double nt = std::floor((n_out[p] + 1 + 255) / 256);
+            const double cols = std::ceil(n_out[p] / nt);
+            const double NT = std::ceil((cols + 1) / 16) * 16;
+            b += 2 * es * bat[p] * nt * NT * K[p];
         }
-        return USR_OK;
-    };
-    usr_status s;
-    if ((s = alloc(&c->d_rho_hi, es * G)) || (s = alloc(&c->d_rho_lo, es * G)) ||
-        (s = alloc(&c->d_X_hi, es * G * N)) || (s = alloc(&c->d_X_lo, es * G * N)) ||
-        (s = alloc(&c->d_Y_hi, es * G * N)) || (s = alloc(&c->d_Y_lo, es * G * N)) ||
-        (s = alloc((void**)&c->d_mu, sizeof(float) * 2 * N)))
-        return s;
-    std::vector<float> mu(2 * N);
-    for (int j = 0; j < N; ++j) {
-        mu[j] = (float)P.mu[0][j];
-        mu[N + j] = (float)P.mu[1][j];
     }
-    if (cudaMemcpy(c->d_mu, mu.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice) != cudaSuccess)
+    return b;
+}
+
+namespace {
+
+/*
+ * Make `c` evaluate the system described by p: plan on the host, grow device
+ * buffers that are too small, and upload the tables through the pinned
+ * staging area with asynchronous copies on `st`.  Buffers already large
+ * enough are reused, so reconfiguring among systems of similar size allocates
+ * nothing and does not synchronise the device.
+ */
+usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
+{
+    Plan np;
+    usr_status s = usr::make_plan(p, &np);
+    if (s != USR_OK) return s;
+    c->plan = np;
+    const Plan& P = c->plan;
+    c->max_atoms = p->max_atoms;
+    c->ncell = P.cells[0] * P.cells[1] * P.cells[2];
+    c->G = (long long)P.n[0] * P.n[1] * P.n[2];
+    c->tc = p->conv == USR_CONV_TF32X3 || p->conv == USR_CONV_BF16X3;
+    c->tc_bf16 = p->conv == USR_CONV_BF16X3;
+    const size_t na = (size_t)(c->max_atoms > 0 ? c->max_atoms : 1);
+    const size_t N = (size_t)P.N, G = (size_t)c->G;
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int nsb = usr::tile_blocks(P.tile);
+    c->max_clusters = (int)((na + 7 * (size_t)c->ncell + 7) / 8);
+    const size_t ncl = (size_t)c->max_clusters;
+    const size_t f4 = sizeof(float4), i4 = sizeof(int), fl = sizeof(float), db = sizeof(double);
+#define ENSURE(ptr, bytes) \
+    if ((s = ensure(c, (void**)&(ptr), (bytes))) != USR_OK) return s;
+    ENSURE(c->d_count, i4 * c->ncell);
+    ENSURE(c->d_cell_start, i4 * (c->ncell + 1));
+    ENSURE(c->d_pstart, i4 * (c->ncell + 1));
+    ENSURE(c->d_cpos, f4 * ncl * 8);
+    ENSURE(c->d_cidx, i4 * ncl * 8);
+    ENSURE(c->d_ccell, i4 * ncl);
+    ENSURE(c->d_bblo, f4 * ncl);
+    ENSURE(c->d_bbhi, f4 * ncl);
+    ENSURE(c->d_cell_of, i4 * na);
+    ENSURE(c->d_slot, i4 * na);
+    ENSURE(c->d_unsorted, i4 * na);
+    ENSURE(c->d_perm, i4 * na);
+    ENSURE(c->d_status, i4);
+    ENSURE(c->d_wpos, f4 * na);
+    ENSURE(c->d_spos, f4 * na);
+    ENSURE(c->d_near, f4 * na);
+    ENSURE(c->d_psi, fl * G);
+    ENSURE(c->d_spread_partial, db * nsb);
+    ENSURE(c->d_mean, db);
+    ENSURE(c->d_gather_partial, db * nsb * 4);
+    ENSURE(c->d_energy, db * 4);
+    ENSURE(c->d_counters, sizeof(unsigned int) * 3);
+    ENSURE(c->d_psi_partial, db * usr::kGridMeanBlocks);
+    ENSURE(c->d_psi_mean, db);
+    ENSURE(c->d_in, f4 * na);
+    ENSURE(c->d_out, f4 * na);
+    ENSURE(c->d_near_dbg, f4 * na);
+    ENSURE(c->d_far_dbg, f4 * na);
+    ENSURE(c->d_tilebuf, fl * nsb * usr::tile_floats(P.tile));
+    for (int a = 0; a < 3; ++a) ENSURE(c->d_tab[a], i4 * tab_ints(P, a));
+    Staged up;
+    if (!c->tc) {
+        ENSURE(c->d_rho, fl * G);
+        ENSURE(c->d_X, fl * N * G);
+        ENSURE(c->d_Y, fl * N * G);
+        ENSURE(c->d_Bx, fl * nx * N * nx);
+        ENSURE(c->d_Ay, fl * N * ny * ny);
+        ENSURE(c->d_Az, fl * nz * N * nz);
+        ENSURE(c->d_wx, fl * N * nx);
+        ENSURE(c->d_wy, fl * N * ny);
+        ENSURE(c->d_wz, fl * N * nz);
+        std::vector<float> Bx((size_t)nx * N * nx), Ay((size_t)N * ny * ny), Az((size_t)nz * N * nz);
+        std::vector<float> wx(N * nx), wy(N * ny), wz(N * nz);
+        for (size_t j = 0; j < N; ++j) {
+            for (int k = 0; k < nx; ++k)
+                for (int m = 0; m < nx; ++m)
+                    Bx[(size_t)k * N * nx + j * nx + m] = (float)P.ktil[0][j][((m - k) % nx + nx) % nx];
+            for (int m = 0; m < ny; ++m)
+                for (int k = 0; k < ny; ++k)
+                    Ay[((size_t)j * ny + m) * ny + k] = (float)P.ktil[1][j][((m - k) % ny + ny) % ny];
+            for (int m = 0; m < nz; ++m)
+                for (int k = 0; k < nz; ++k)
+                    Az[(size_t)m * N * nz + j * nz + k] =
+                        (float)(P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz]);
+            for (int m = 0; m < nx; ++m) wx[j * nx + m] = (float)P.mu[0][j];
+            for (int k = 0; k < ny; ++k) wy[j * ny + k] = (float)P.mu[1][j];
+            for (int k = 0; k < nz; ++k) wz[j * nz + k] = (float)(P.scale[j] * P.mu[2][j]);
+        }
+        up.add(c->d_Bx, Bx.data(), Bx.size());
+        up.add(c->d_Ay, Ay.data(), Ay.size());
+        up.add(c->d_Az, Az.data(), Az.size());
+        up.add(c->d_wx, wx.data(), wx.size());
+        up.add(c->d_wy, wy.data(), wy.size());
+        up.add(c->d_wz, wz.data(), wz.size());
+    }
+    fill_args(c);
+    // per axis: tile origins, then reduction counts, then (block, offset) pairs
+    for (int a = 0; a < 3; ++a) {
+        std::vector<int> t;
+        t.insert(t.end(), P.tile_org[a].begin(), P.tile_org[a].end());
+        t.insert(t.end(), P.red_cnt[a].begin(), P.red_cnt[a].end());
+        while (t.size() % 2) t.push_back(0);
+        t.insert(t.end(), P.red_pair[a].begin(), P.red_pair[a].end());
+        up.add(c->d_tab[a], t.data(), t.size());
+        const size_t off_cnt = P.tile_org[a].size();
+        const size_t off_pair = (off_cnt + P.red_cnt[a].size() + 1) / 2 * 2;
+        c->grid.tab.org[a] = c->d_tab[a];
+        c->grid.tab.red_cnt[a] = c->d_tab[a] + off_cnt;
+        c->grid.tab.red_pair[a] = reinterpret_cast<const int2*>(c->d_tab[a] + off_pair);
+    }
+    c->grid.psi_mean = c->d_psi_mean;
+    if (c->tc) {
+        const bool bf = c->tc_bf16;
+        const size_t es = bf ? 2 : 4;
+        ENSURE(c->d_rho_hi, es * G);
+        ENSURE(c->d_rho_lo, es * G);
+        ENSURE(c->d_X_hi, es * G * N);
+        ENSURE(c->d_X_lo, es * G * N);
+        ENSURE(c->d_Y_hi, es * G * N);
+        ENSURE(c->d_Y_lo, es * G * N);
+        ENSURE(c->d_mu, fl * 2 * N);
+        std::vector<float> mu(2 * N);
+        for (size_t j = 0; j < N; ++j) {
+            mu[j] = (float)P.mu[0][j];
+            mu[N + j] = (float)P.mu[1][j];
+        }
+        up.add(c->d_mu, mu.data(), mu.size());
+        const int n_out[3] = {nx, ny, nz};
+        const int Ks[3] = {nx, ny, (int)N * nz};
+        const int lines[3] = {ny * nz, nx * nz, ny * nx};
+        const int batches[3] = {(int)N, (int)N, 1};
+        const long long a_rows[3] = {(long long)ny * nz, (long long)N * nx * nz, (long long)ny * nx};
+        for (int ps = 0; ps < 3; ++ps) {
+            usr::ConvTcArgs& a = c->targs[ps];
+            std::memset(&a, 0, sizeof(a));
+            tc_shape(a, n_out[ps], Ks[ps], bf);
+            std::vector<double> B = tc_table(P, ps + 1, a, batches[ps]);
+            ENSURE(c->d_Bt_hi[ps], es * B.size());
+            ENSURE(c->d_Bt_lo[ps], es * B.size());
+            if (bf) {
+                std::vector<__nv_bfloat16> h(B.size()), l(B.size());
+                for (size_t i = 0; i < B.size(); ++i) {
+                    h[i] = __float2bfloat16_rn((float)B[i]);
+                    l[i] = __float2bfloat16_rn((float)(B[i] - (double)__bfloat162float(h[i])));
+                }
+                up.add(c->d_Bt_hi[ps], h.data(), h.size());
+                up.add(c->d_Bt_lo[ps], l.data(), l.size());
+            } else {
+                std::vector<float> h(B.size()), l(B.size());
+                for (size_t i = 0; i < B.size(); ++i) {
+                    h[i] = tf32_rna((float)B[i]);
+                    l[i] = tf32_rna((float)(B[i] - (double)h[i]));
+                }
+                up.add(c->d_Bt_hi[ps], h.data(), h.size());
+                up.add(c->d_Bt_lo[ps], l.data(), l.size());
+            }
+        }
+        void* a_hi[3] = {c->d_rho_hi, c->d_X_hi, c->d_Y_hi};
+        void* a_lo[3] = {c->d_rho_lo, c->d_X_lo, c->d_Y_lo};
+        void* o_hi[3] = {c->d_X_hi, c->d_Y_hi, c->d_psi};
+        void* o_lo[3] = {c->d_X_lo, c->d_Y_lo, nullptr};
+        for (int ps = 0; ps < 3; ++ps) {
+            usr::ConvTcArgs& a = c->targs[ps];
+            a.pass = ps + 1;
+            a.lines = lines[ps];
+            a.a_rows_per_batch = ps == 1 ? nx * nz : 0;
+            a.nterms = (int)N;
+            a.nx = nx;
+            a.ny = ny;
+            a.nz = nz;
+            a.mu = ps == 0 ? c->d_mu : (ps == 1 ? c->d_mu + N : nullptr);
+            a.out_hi = o_hi[ps];
+            a.out_lo = o_lo[ps];
+            a.status = c->d_status;
+            c->tbatches[ps] = batches[ps];
+            const long long b_rows = (long long)batches[ps] * a.ntiles * a.NT;
+            if ((s = usr::make_tmap(&c->maps[ps].a_hi, a_hi[ps], bf, a_rows[ps], a.K, 128)) ||
+                (s = usr::make_tmap(&c->maps[ps].a_lo, a_lo[ps], bf, a_rows[ps], a.K, 128)) ||
+                (s = usr::make_tmap(&c->maps[ps].b_hi, c->d_Bt_hi[ps], bf, b_rows, a.K, a.NT)) ||
+                (s = usr::make_tmap(&c->maps[ps].b_lo, c->d_Bt_lo[ps], bf, b_rows, a.K, a.NT)))
+                return s;
+        }
+    }
+#undef ENSURE
+    {   // what the context holds (buffers only grow, so this can exceed the plan's own need)
+        double held = 0.0;
+        for (const auto& kv : c->cap) held += (double)kv.second;
+        c->plan.info.device_bytes = held;
+    }
+    // staged upload: wait until the previous upload has left the staging area
+    if (c->stage_ev && cudaEventSynchronize(c->stage_ev) != cudaSuccess) return USR_ERR_CUDA;
+    if (up.bytes.size() > c->stage_cap) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->stage_cap = 0;
+        if (cudaHostAlloc((void**)&c->h_stage, up.bytes.size(), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return USR_ERR_OOM;
+        }
+        c->stage_cap = up.bytes.size();
+    }
+    std::memcpy(c->h_stage, up.bytes.data(), up.bytes.size());
+    for (const auto& it : up.items)
+        if (cudaMemcpyAsync(it.dst, c->h_stage + it.off, it.len, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return USR_ERR_CUDA;
+    if (!c->stage_ev && cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess)
         return USR_ERR_CUDA;
-    const int n_out[3] = {nx, ny, nz};
-    const int Ks[3] = {nx, ny, N * nz};
-    const int lines[3] = {ny * nz, nx * nz, ny * nx};
-    const int batches[3] = {N, N, 1};
-    const long long a_rows[3] = {(long long)ny * nz, (long long)N * nx * nz, (long long)ny * nx};
-    void* a_hi[3] = {c->d_rho_hi, c->d_X_hi, c->d_Y_hi};
-    void* a_lo[3] = {c->d_rho_lo, c->d_X_lo, c->d_Y_lo};
-    void* o_hi[3] = {c->d_X_hi, c->d_Y_hi, c->d_psi};
-    void* o_lo[3] = {c->d_X_lo, c->d_Y_lo, nullptr};
-    for (int p = 0; p < 3; ++p) {
-        usr::ConvTcArgs& a = c->targs[p];
-        std::memset(&a, 0, sizeof(a));
-        tc_shape(a, n_out[p], Ks[p], bf);
-        a.pass = p + 1;
-        a.lines = lines[p];
-        a.a_rows_per_batch = p == 1 ? nx * nz : 0;
-        a.nterms = N;
-        a.nx = nx;
-        a.ny = ny;
-        a.nz = nz;
-        a.mu = p == 0 ? c->d_mu : (p == 1 ? c->d_mu + N : nullptr);
-        a.out_hi = o_hi[p];
-        a.out_lo = o_lo[p];
-        a.status = c->d_status;
-        c->tbatches[p] = batches[p];
-        std::vector<double> B = tc_table(P, p + 1, a, batches[p]);
-        if ((s = alloc(&c->d_Bt_hi[p], es * B.size())) || (s = alloc(&c->d_Bt_lo[p], es * B.size())) ||
-            (s = upload_split(B, bf, c->d_Bt_hi[p], c->d_Bt_lo[p])))
-            return s;
-        const long long b_rows = (long long)batches[p] * a.ntiles * a.NT;
-        if ((s = usr::make_tmap(&c->maps[p].a_hi, a_hi[p], bf, a_rows[p], a.K, 128)) ||
-            (s = usr::make_tmap(&c->maps[p].a_lo, a_lo[p], bf, a_rows[p], a.K, 128)) ||
-            (s = usr::make_tmap(&c->maps[p].b_hi, c->d_Bt_hi[p], bf, b_rows, a.K, a.NT)) ||
-            (s = usr::make_tmap(&c->maps[p].b_lo, c->d_Bt_lo[p], bf, b_rows, a.K, a.NT)))
-            return s;
-        // keep (CTAs per SM) x (TMEM columns) <= 512 by padding the shared memory request
-        const size_t floor_smem = (size_t)228 * 1024 * a.tmem_cols / 512 + 1024;
-        a.smem = (int)std::max(usr::conv_tc_smem(a), floor_smem);
-        if ((s = usr::conv_tc_setup(bf, (size_t)a.smem)) != USR_OK) return s;
-    }
+    if (cudaEventRecord(c->stage_ev, st) != cudaSuccess) return USR_ERR_CUDA;
     return USR_OK;
 }
 
@@ -467,102 +617,48 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     if (!p) return USR_ERR_ARG;
     usr_ctx* c = new (std::nothrow) usr_ctx();
     if (!c) return USR_ERR_OOM;
-    usr_status s = usr::make_plan(p, &c->plan);
-    if (s != USR_OK) {
+    usr_status s = USR_OK;
+    auto fail = [&](usr_status e) {
+        free_all(c);
         delete c;
-        return s;
+        return e;
+    };
+    {
+        Plan probe;
+        if ((s = usr::make_plan(p, &probe)) != USR_OK) {
+            delete c;
+            return s;
+        }
     }
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return USR_ERR_CUDA;
     }
-    const Plan& P = c->plan;
-    c->max_atoms = p->max_atoms;
-    c->ncell = P.cells[0] * P.cells[1] * P.cells[2];
-    c->G = (long long)P.n[0] * P.n[1] * P.n[2];
-    const size_t na = (size_t)(c->max_atoms > 0 ? c->max_atoms : 1);
-    const size_t N = (size_t)P.N;
-    const int nsb = usr::tile_blocks(P.tile);
-    const int ngb = nsb;
-    fill_args(c);
-#define ALLOC(ptr, cnt) \
-    if ((s = dalloc(&(ptr), (cnt))) != USR_OK) { free_all(c); delete c; return s; }
-    ALLOC(c->d_count, (size_t)c->ncell);
-    ALLOC(c->d_cell_start, (size_t)c->ncell + 1);
-    c->max_clusters = (int)((na + 7 * (size_t)c->ncell + 7) / 8);
-    ALLOC(c->d_pstart, (size_t)c->ncell + 1);
-    ALLOC(c->d_cpos, (size_t)c->max_clusters * 8);
-    ALLOC(c->d_cidx, (size_t)c->max_clusters * 8);
-    ALLOC(c->d_ccell, (size_t)c->max_clusters);
-    ALLOC(c->d_bblo, (size_t)c->max_clusters);
-    ALLOC(c->d_bbhi, (size_t)c->max_clusters);
-    ALLOC(c->d_cell_of, na);
-    ALLOC(c->d_slot, na);
-    ALLOC(c->d_unsorted, na);
-    ALLOC(c->d_perm, na);
-    ALLOC(c->d_status, 1);
-    ALLOC(c->d_wpos, na);
-    ALLOC(c->d_spos, na);
-    ALLOC(c->d_near, na);
-    ALLOC(c->d_rho, (size_t)c->G);
-    ALLOC(c->d_X, N * (size_t)c->G);
-    ALLOC(c->d_Y, N * (size_t)c->G);
-    ALLOC(c->d_psi, (size_t)c->G);
-    ALLOC(c->d_Bx, (size_t)P.n[0] * N * P.n[0]);
-    ALLOC(c->d_Ay, N * P.n[1] * P.n[1]);
-    ALLOC(c->d_Az, (size_t)P.n[2] * N * P.n[2]);
-    ALLOC(c->d_wx, N * P.n[0]);
-    ALLOC(c->d_wy, N * P.n[1]);
-    ALLOC(c->d_wz, N * P.n[2]);
-    ALLOC(c->d_spread_partial, (size_t)nsb);
-    ALLOC(c->d_mean, 1);
-    ALLOC(c->d_gather_partial, (size_t)ngb * 4);
-    ALLOC(c->d_energy, 4);
-    ALLOC(c->d_counters, 3);
-    ALLOC(c->d_psi_partial, (size_t)usr::kGridMeanBlocks);
-    ALLOC(c->d_psi_mean, 1);
-    ALLOC(c->d_in, na);
-    ALLOC(c->d_out, na);
-    ALLOC(c->d_near_dbg, na);
-    ALLOC(c->d_far_dbg, na);
-    ALLOC(c->d_tilebuf, (size_t)nsb * usr::tile_floats(P.tile));
-    for (int a = 0; a < 3; ++a) ALLOC(c->d_tab[a], tab_ints(P, a));
-#undef ALLOC
-    c->grid.psi_mean = c->d_psi_mean;
+    if ((s = usr::grid_kernel_setup(usr::kTileMaxSmem)) != USR_OK) return fail(s);
+    if ((s = usr::conv_tc_setup(false, usr::kConvTcMaxSmem)) != USR_OK ||
+        (s = usr::conv_tc_setup(true, usr::kConvTcMaxSmem)) != USR_OK)
+        return fail(s);
+    if ((s = configure(c, p, 0)) != USR_OK) return fail(s);
     if (cudaMemset(c->d_counters, 0, 3 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess) {
-        free_all(c);
-        delete c;
-        return USR_ERR_CUDA;
-    }
-    if ((s = usr::grid_kernel_setup(P.P, P.tile)) != USR_OK) {
-        free_all(c);
-        delete c;
-        return s;
-    }
-    if ((s = upload_tables(c)) != USR_OK) {
-        free_all(c);
-        delete c;
-        return s;
-    }
-    c->tc = p->conv == USR_CONV_TF32X3 || p->conv == USR_CONV_BF16X3;
-    c->tc_bf16 = p->conv == USR_CONV_BF16X3;
-    if (c->tc && (s = setup_tc(c)) != USR_OK) {
-        free_all(c);
-        delete c;
-        return s;
-    }
+        cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess)
+        return fail(USR_ERR_CUDA);
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->ev_made = true;
-    if (cudaDeviceSynchronize() != cudaSuccess) {
-        free_all(c);
-        delete c;
-        return USR_ERR_CUDA;
-    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(USR_ERR_CUDA);
     *out = c;
     return USR_OK;
+}
+
+extern "C" usr_status usr_reconfigure(usr_ctx* c, const usr_params* p, void* stream)
+{
+    if (!c || !p) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    c->parts_valid = false;
+    c->prof_valid = false;
+    return configure(c, p, (cudaStream_t)stream);
 }
 
 extern "C" void usr_destroy(usr_ctx* c)
@@ -608,6 +704,26 @@ extern "C" usr_status usr_eval_host(usr_ctx* c, int n, const float* xyzq, float*
     if (energy && cudaMemcpyAsync(energy, c->d_energy, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return USR_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? USR_OK : USR_ERR_CUDA;
+}
+
+extern "C" usr_status usr_eval_host_async(usr_ctx* c, int n, const float* xyzq, float* out, double* energy,
+                                         void* stream)
+{
+    if (!c || n < 0) return USR_ERR_ARG;
+    if (n > c->max_atoms) return USR_ERR_CAPACITY;
+    if (n > 0 && (!xyzq || !out)) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0 && cudaMemcpyAsync(c->d_in, xyzq, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    s = run_eval(c, n, c->d_in, c->d_out, c->d_energy, st);
+    if (s != USR_OK) return s;
+    if (n > 0 && cudaMemcpyAsync(out, c->d_out, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    if (energy && cudaMemcpyAsync(energy, c->d_energy, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return USR_ERR_CUDA;
+    return USR_OK;
 }
 
 extern "C" usr_status usr_last_device_status(usr_ctx* c)

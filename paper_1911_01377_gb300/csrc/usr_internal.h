@@ -78,6 +78,9 @@ struct Plan {
 /* Build the plan (host only).  Returns USR_OK or an error. */
 usr_status make_plan(const usr_params* p, Plan* out);
 
+/* Device bytes a context holds for a plan (the buffers of usr_api.cu's configure). */
+double plan_device_bytes(const Plan& P);
+
 /* Canonical single-precision box constants per axis (see the oracle's predicate). */
 struct BoxF {
     float L[3];       // (float)L
@@ -124,6 +127,7 @@ struct ConvGemm {
 
 /* One pass of the tensor-core convolutions (k_conv_tc.cu). */
 constexpr int kConvTcMaxStages = 6;
+constexpr size_t kConvTcMaxSmem = 220 * 1024;   // dynamic part; static shared memory needs the rest
 struct ConvTcArgs {
     int pass;               // 1 = x, 2 = y, 3 = z
     int lines;              // valid A rows (output lines) per batch
@@ -174,6 +178,6 @@ void launch_gather(int P, const float4* spos, const int* cell_start, const int* 
                    cudaStream_t st);
 int tile_blocks(const TileGeom& tg);
 size_t tile_floats(const TileGeom& tg);
-usr_status grid_kernel_setup(int P, const TileGeom& tg);
+usr_status grid_kernel_setup(size_t smem_bytes);
 
 }  // namespace usr

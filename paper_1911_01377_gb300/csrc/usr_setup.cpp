@@ -248,7 +248,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     P.expl.assign(P.a.size(), 0);
     for (size_t j = 0; j < P.a.size() && P.n_explicit < kMaxExplicit; ++j) {
         double range = rc2 / (2.0 * P.s[j] * P.s[j]);
-        if (range > 2.5) {
+        if (range > 1.5) {
             P.expl[j] = 1;
             P.ea[P.n_explicit] = P.a[j];
             P.einv[P.n_explicit] = 1.0 / (2.0 * P.s[j] * P.s[j]);
@@ -312,13 +312,15 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             }
         }
     }
-    static const int kDegs[] = {8, 10, 12, 16, 20, 24};
+    // the pair kernel evaluates F in FP32 (relative rounding ~6e-8): a fit error
+    // well below that is enough
+    static const int kDegs[] = {6, 7, 8, 10, 12, 16, 20, 24};
     P.poly_deg = 0;
     double ev = 1.0, ed = 1.0;
     for (int D : kDegs) {
         fit_poly(P, D, P.poly, &ev, &ed);
         P.poly_deg = D;
-        if (ev < 1e-10 && ed < 1e-8) break;
+        if (ev < 2e-9 && ed < 1e-7) break;
     }
     for (int i = P.poly_deg + 1; i <= kMaxPolyDeg; ++i) P.poly[i] = 0.0;
 
@@ -356,7 +358,10 @@ extern "C" usr_status usr_plan(const usr_params* p, usr_plan_info* out)
     if (!p || !out) return USR_ERR_ARG;
     usr::Plan* P = new usr::Plan();
     usr_status st = usr::make_plan(p, P);
-    if (st == USR_OK) *out = P->info;
+    if (st == USR_OK) {
+        *out = P->info;
+        out->device_bytes = usr::plan_device_bytes(*P);
+    }
     delete P;
     return st;
 }

@@ -35,7 +35,11 @@ class usr_params(ctypes.Structure):
 class usr_plan_info(ctypes.Structure):
     _fields_ = [("sigma", _c_d), ("F0", _c_d), ("spread_sigma", _c_d), ("h", _c_d * 3), ("trunc_bound", _c_d),
                 ("n_terms", _c_i), ("cells", _c_i * 3), ("poly_degree", _c_i), ("n_explicit", _c_i),
-                ("poly_max_err", _c_d)]
+                ("poly_max_err", _c_d), ("device_bytes", _c_d)]
+
+
+class usr_server_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", _c_d), ("slots", _c_i)]
 
 
 class UsrError(RuntimeError):
@@ -57,6 +61,7 @@ def lib():
         L.usr_series_preset.argtypes = [_c_i, ctypes.POINTER(usr_series)]
         L.usr_plan.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(usr_plan_info)]
         L.usr_init.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(_c_p)]
+        L.usr_reconfigure.argtypes = [_c_p, ctypes.POINTER(usr_params), _c_p]
         L.usr_destroy.argtypes = [_c_p]
         L.usr_destroy.restype = None
         L.usr_info.argtypes = [_c_p, ctypes.POINTER(usr_plan_info)]
@@ -69,13 +74,27 @@ def lib():
         L.usr_debug_pairs.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
         L.usr_cells_static.argtypes = [_c_i, _c_p, ctypes.POINTER(_c_d), ctypes.POINTER(_c_i), _c_p, _c_p, _c_p,
                                        _c_p, _c_p]
+        L.usr_eval_host_async.argtypes = [_c_p, _c_i, _c_p, _c_p, _c_p, _c_p]
+        L.usr_server_create.argtypes = [ctypes.POINTER(usr_server_params), ctypes.POINTER(_c_p)]
+        L.usr_server_submit.argtypes = [_c_p, ctypes.POINTER(usr_params), _c_i, _c_p, _c_p, _c_p,
+                                        ctypes.POINTER(ctypes.c_longlong)]
+        L.usr_server_poll.argtypes = [_c_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_c_d),
+                                      ctypes.POINTER(_c_i), _c_i]
+        L.usr_server_poll.restype = _c_i
+        L.usr_server_wait.argtypes = [_c_p, _c_d]
+        L.usr_server_info.argtypes = [_c_p, ctypes.POINTER(_c_d), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong)]
+        L.usr_server_destroy.argtypes = [_c_p]
+        L.usr_server_destroy.restype = None
         L.usr_set_keep_parts.argtypes = [_c_p, _c_i]
         L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
         L.usr_stage_times.argtypes = [_c_p, ctypes.POINTER(ctypes.c_float)]
-        for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_info", "usr_eval", "usr_eval_host",
+        for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
+                     "usr_eval_host",
                      "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
-                     "usr_set_keep_parts",
+                     "usr_set_keep_parts", "usr_eval_host_async", "usr_server_create", "usr_server_submit",
+                     "usr_server_wait", "usr_server_info",
                      "usr_debug_parts", "usr_set_profiling", "usr_stage_times"):
             getattr(L, name).restype = _c_i
         _lib = L
@@ -130,6 +149,10 @@ def usr_init(params: usr_params) -> int:
     h = _c_p()
     _check(lib().usr_init(ctypes.byref(params), ctypes.byref(h)), "usr_init")
     return h.value
+
+
+def usr_reconfigure(ctx: int, params: usr_params, stream=None):
+    _check(lib().usr_reconfigure(ctx, ctypes.byref(params), _stream_ptr(stream)), "usr_reconfigure")
 
 
 def usr_destroy(ctx: int):
@@ -208,6 +231,13 @@ class USeries:
         self.info = usr_info(self.ctx)
         self.max_atoms = max_atoms
 
+    def reconfigure(self, box, grid, r_c, series="C1_B2", max_atoms=0, stream=None, **kw):
+        """Point this context at another system (usr_reconfigure)."""
+        self.params = make_params(box, grid, r_c, series, max_atoms=max_atoms, **kw)
+        usr_reconfigure(self.ctx, self.params, stream)
+        self.info = usr_info(self.ctx)
+        self.max_atoms = max_atoms
+
     def close(self):
         if self.ctx:
             usr_destroy(self.ctx)
@@ -269,3 +299,62 @@ class USeries:
         far = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         usr_debug_parts(self.ctx, near.data_ptr(), far.data_ptr())
         return near, far
+
+
+class Server:
+    """Continuous-batching server (usr_server_*): independent systems evaluated
+    as they arrive, up to `slots` at once within `hbm_budget_bytes`.
+
+    submit() takes pinned host tensors and keeps them referenced until the
+    request completes; poll() returns (ticket, latency_ms, status) tuples.
+    """
+
+    def __init__(self, hbm_budget_bytes=0.0, slots=0):
+        p = usr_server_params(float(hbm_budget_bytes), int(slots))
+        h = _c_p()
+        _check(lib().usr_server_create(ctypes.byref(p), ctypes.byref(h)), "usr_server_create")
+        self.handle = h.value
+        self._live = {}
+
+    def submit(self, params: usr_params, xyzq, out, energy=None) -> int:
+        n = int(xyzq.shape[0])
+        t = ctypes.c_longlong(0)
+        _check(lib().usr_server_submit(self.handle, ctypes.byref(params), n, xyzq.data_ptr(), out.data_ptr(),
+                                       energy.data_ptr() if energy is not None else None, ctypes.byref(t)),
+               "usr_server_submit")
+        self._live[t.value] = (params, xyzq, out, energy)
+        return t.value
+
+    def poll(self, max_n=1024):
+        tk = (ctypes.c_longlong * max_n)()
+        lat = (_c_d * max_n)()
+        st = (_c_i * max_n)()
+        k = lib().usr_server_poll(self.handle, tk, lat, st, max_n)
+        res = []
+        for i in range(k):
+            self._live.pop(tk[i], None)
+            res.append((int(tk[i]), float(lat[i]), int(st[i])))
+        return res
+
+    def wait(self, timeout_s=0.0):
+        _check(lib().usr_server_wait(self.handle, float(timeout_s)), "usr_server_wait")
+
+    def info(self):
+        b = _c_d(0.0)
+        q = ctypes.c_longlong(0)
+        f = ctypes.c_longlong(0)
+        _check(lib().usr_server_info(self.handle, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)),
+               "usr_server_info")
+        return float(b.value), int(q.value), int(f.value)
+
+    def close(self):
+        if self.handle:
+            lib().usr_server_destroy(self.handle)
+            self.handle = 0
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -314,6 +314,50 @@ def get(name: str) -> Workload:
     return w
 
 
+def lattice_water_box(seed: int, n_charges: int, density: float = 0.1) -> Tuple[Tuple[float, float, float], np.ndarray]:
+    """A cubic water box of n_charges (a multiple of 3) at `density` charges per A^3,
+    generated fast for serving streams: O centres on randomly chosen sites of a
+    periodic cubic lattice (spacing ~3.1 A at water density) with a jitter of at
+    most 0.25 A per axis, so that O-O distances stay >= 2.5 A without rejection;
+    uniformly random orientations.  Returns (box, xyzq)."""
+    rng = np.random.default_rng(seed)
+    n_w = n_charges // 3
+    L = (3 * n_w / density) ** (1.0 / 3.0)
+    m = int(math.ceil(n_w ** (1.0 / 3.0) - 1e-9))
+    a = L / m
+    if a < 2.5:
+        raise ValueError("lattice too dense for the O-O separation")
+    jit = min(0.25, 0.5 * (a - 2.5))            # keeps O-O >= 2.5 A
+    sites = rng.choice(m ** 3, size=n_w, replace=False)
+    iz, rem = np.divmod(sites, m * m)
+    iy, ix = np.divmod(rem, m)
+    centres = (np.stack([ix, iy, iz], axis=1) + 0.5) * a + rng.uniform(-jit, jit, size=(n_w, 3))
+    R = random_rotations(rng, n_w)
+    half = 0.5 * THETA_HOH
+    local = np.array([[0.0, 0.0, 0.0],
+                      [R_OH * math.sin(half), 0.0, R_OH * math.cos(half)],
+                      [-R_OH * math.sin(half), 0.0, R_OH * math.cos(half)]])
+    sites_xyz = centres[:, None, :] + np.einsum("nij,kj->nki", R, local)
+    q = np.tile(np.array([Q_O, Q_H, Q_H]), (n_w, 1))
+    rows = np.concatenate([sites_xyz.reshape(-1, 3), q.reshape(-1, 1)], axis=1)
+    return (L, L, L), np.ascontiguousarray(rows.astype(np.float32))
+
+
+def serving_stream(seed: int, count: int, n_min: int = 2000, n_max: int = 200000, density: float = 0.1,
+                   spacing: float = 1.0, r_c: float = 9.0, grid_multiple: int = 8):
+    """The serving workload: `count` independent water boxes with charge counts
+    log-uniform in [n_min, n_max] (multiples of 3), cubic boxes sized to the
+    density, grids of about `spacing` A rounded to a multiple of grid_multiple.
+    Yields (box, grid, r_c, xyzq) lazily (generation is the slow part)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=count))
+    for k, nf in enumerate(ns):
+        n = max(3, int(round(nf / 3.0)) * 3)
+        box, xyzq = lattice_water_box(seed * 1000 + k, n, density)
+        g = max(grid_multiple * 3, int(round(box[0] / spacing / grid_multiple)) * grid_multiple)
+        yield box, (g, g, g), r_c, xyzq
+
+
 def random_neutral(seed: int, n: int, box, qscale: float = 1.0, min_dist: float = 0.0) -> np.ndarray:
     """n random charges (float32 rows) in a box, charges shifted to sum to zero."""
     rng = np.random.default_rng(seed)

@@ -330,3 +330,39 @@ def test_repeatable(torch_cuda, name, r_c):
     torch.cuda.synchronize()
     assert np.array_equal(o1.cpu().numpy(), o2.cpu().numpy())
     assert np.array_equal(e1.cpu().numpy(), e2.cpu().numpy())
+
+
+@pytest.mark.parametrize("conv", [0, 2])
+def test_cuda_graph_capture_and_replay(torch_cuda, conv):
+    # usr_eval enqueues kernels and copies only (no allocation, no host
+    # synchronisation), so it can be captured in a CUDA graph and replayed;
+    # replays pick up new positions written into the same input buffer
+    torch = torch_cuda
+    w = workload("water_3k")
+    ctx = usr.USeries(w.box, w.grid, 9.0, "C1_B2", max_atoms=w.n, conv=conv)
+    x = torch.from_numpy(w.xyzq).cuda()
+    out = torch.empty((w.n, 4), dtype=torch.float32, device="cuda")
+    en = torch.empty(4, dtype=torch.float64, device="cuda")
+    ctx.eval(x, out, en)
+    torch.cuda.synchronize()
+    ref_o, ref_e = out.clone(), en.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            usr.usr_eval(ctx.ctx, w.n, x.data_ptr(), out.data_ptr(), en.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    out.zero_()
+    en.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref_o) and torch.equal(en, ref_e)
+    moved = w.xyzq.copy()
+    moved[:, :3] += np.float32(0.37)
+    x.copy_(torch.from_numpy(moved))
+    g.replay()
+    torch.cuda.synchronize()
+    o2, e2 = ctx.eval(torch.from_numpy(moved).cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(out, o2) and torch.equal(en, e2)
