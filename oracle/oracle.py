@@ -55,6 +55,10 @@ def lib():
         L.or_far_realspace.restype = _i
         L.or_eval.argtypes = sp + [_pd, _i, _d, _i, _pd, _pd, _i, _pi, _pd, _pd, _pd, _pd, _pd, _pd, _pd]
         L.or_eval.restype = _i
+        L.or_virial.argtypes = sp + [_pd, _i, _d, _i, _pd, _pd, _pd, _pd]
+        L.or_virial.restype = _i
+        L.or_far_virial_realspace.argtypes = sp + [_pd, _i, _i, _pd, _pd, _pd]
+        L.or_far_virial_realspace.restype = _i
         L.or_ewald.argtypes = [_pd, _d, _d, _d, _i, _pd, _pd, _pd, _pd, _pd]
         L.or_ewald.restype = _i
         L.or_canon_cells.argtypes = [_i, _pf, _pd, _pi, _pi, _pf]
@@ -185,6 +189,25 @@ def evaluate(series: Series, r_c, box, pos, q, targets=None, n_terms: int = 0,
     return Result(en[0], en[1], en[2], en[3], phi, f, pn, fn, pf, ff)
 
 
+def virial(series: Series, r_c, box, pos, q, n_terms: int = 0, kmax: float = 0.0):
+    """Virial tensor -dE/d(strain): (W_near, W_far) as 3 x 3 arrays (the self term adds none)."""
+    box, pos, q = _prep(box, pos, q)
+    wn = np.zeros(9)
+    wf = np.zeros(9)
+    rc = lib().or_virial(*series, r_c, _dp(box), n_terms, kmax, q.size, _dp(pos), _dp(q), _dp(wn), _dp(wf))
+    assert rc == 0
+    return wn.reshape(3, 3), wf.reshape(3, 3)
+
+
+def far_virial_realspace(series: Series, r_c, box, pos, q, n_terms: int):
+    """Far-part virial of the first n_terms Gaussians as a real-space image sum (tiny systems)."""
+    box, pos, q = _prep(box, pos, q)
+    wf = np.zeros(9)
+    rc = lib().or_far_virial_realspace(*series, r_c, _dp(box), n_terms, q.size, _dp(pos), _dp(q), _dp(wf))
+    assert rc == 0
+    return wf.reshape(3, 3)
+
+
 def ewald(box, pos, q, sigma_e: Optional[float] = None, tol: float = 1e-16):
     """Classic Ewald sum (Eqs. 6-10); returns (E, phi, f)."""
     box, pos, q = _prep(box, pos, q)
@@ -237,4 +260,5 @@ def rms_rel(a, ref) -> float:
 
 
 __all__ = ["Series", "lib", "num_threads", "terms", "far_function", "far_fhat", "F0", "near", "far",
-           "far_realspace", "Result", "evaluate", "ewald", "canon_cells", "canon_pairs", "rms_rel"]
+           "far_realspace", "Result", "evaluate", "ewald", "canon_cells", "canon_pairs", "rms_rel", "virial",
+           "far_virial_realspace"]

@@ -540,6 +540,183 @@ int or_eval(double b, double r0, double w0, double s0, double r_c, const double*
     return rc;
 }
 
+/* ----------------------------------------------------------------- virial */
+
+/* sum_j s_j^2 Fhat_j(k): the strain derivative weight of the far part. */
+static double far_Fhat_s2(const or_terms* t, double k, int nk)
+{
+    int n = (nk > 0 && nk < t->n) ? nk : t->n;
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s2 = t->s[j] * t->s[j];
+        double x = 0.5 * s2 * k * k;
+        if (x > 745.0) continue;
+        sum += s2 * t->a[j] * pow(2.0 * M_PI * s2, 1.5) * exp(-x);
+    }
+    return sum;
+}
+
+/*
+ * Virial tensor W = -dE/d(strain) under an affine strain of positions and box
+ * (row-major 3 x 3, symmetric).
+ *   near:  W = 1/2 sum_{i != j, images, r < r_c} d (x) f_ij,  f_ij = q_i q_j (1/r^3 + F'(r)/r) d
+ *          (the pair force of Eq. 20's near function on i, d = r_i - r_j - image)
+ *   far:   W_ab = delta_ab E_far - (1/2V) sum_{k != 0} |S(k)|^2 k_a k_b sum_j s_j^2 Fhat_j(k)
+ *          (the strain derivative of Eq. F1: V grows with the trace, k shrinks as the box grows,
+ *           and dFhat_j/d(k^2) = -s_j^2 Fhat_j / 2)
+ *   self:  no box dependence (F(0) is fixed by sigma), no contribution.
+ * n_terms / kmax as in or_far.
+ */
+int or_virial(double b, double r0, double w0, double s0, double r_c, const double* box,
+              int n_terms, double kmax, int n, const double* pos, const double* q,
+              double* W_near, double* W_far)
+{
+    or_terms* t = (or_terms*)malloc(sizeof(or_terms));
+    if (!t) return -1;
+    build_terms(b, r0, w0, s0, r_c, t);
+    /* near: direct pair sum */
+    double* w = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!w) { free(t); return -1; }
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) w[3 * i + a] = wrap1(pos[3 * i + a], box[a]);
+    int M[3];
+    for (int a = 0; a < 3; ++a) M[a] = (r_c < 0.5 * box[a]) ? 0 : (int)ceil(r_c / box[a]);
+    double rc2 = r_c * r_c;
+    double wn[6] = {0, 0, 0, 0, 0, 0};   /* xx yy zz xy xz yz */
+#pragma omp parallel
+    {
+        double loc[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                double dx0 = minimg(w[3 * i] - w[3 * j], box[0]);
+                double dy0 = minimg(w[3 * i + 1] - w[3 * j + 1], box[1]);
+                double dz0 = minimg(w[3 * i + 2] - w[3 * j + 2], box[2]);
+                for (int mx = -M[0]; mx <= M[0]; ++mx)
+                    for (int my = -M[1]; my <= M[1]; ++my)
+                        for (int mz = -M[2]; mz <= M[2]; ++mz) {
+                            if (i == j && mx == 0 && my == 0 && mz == 0) continue;
+                            double dx = dx0 + mx * box[0], dy = dy0 + my * box[1], dz = dz0 + mz * box[2];
+                            double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 >= rc2) continue;
+                            double r = sqrt(r2), dFr = 0.0;
+                            for (int k = t->n - 1; k >= 0; --k) {
+                                double s2 = t->s[k] * t->s[k];
+                                dFr -= t->a[k] * exp(-r2 / (2.0 * s2)) / s2;
+                            }
+                            double g = 0.5 * q[i] * q[j] * (1.0 / (r2 * r) + dFr);
+                            loc[0] += g * dx * dx; loc[1] += g * dy * dy; loc[2] += g * dz * dz;
+                            loc[3] += g * dx * dy; loc[4] += g * dx * dz; loc[5] += g * dy * dz;
+                        }
+            }
+        }
+#pragma omp critical
+        for (int c = 0; c < 6; ++c) wn[c] += loc[c];
+    }
+    free(w);
+    /* far: k-space */
+    if (kmax <= 0.0) {
+        double smin = t->s[0];
+        for (int j = 1; j < t->n; ++j) if (t->s[j] < smin) smin = t->s[j];
+        kmax = 9.2 / smin;
+    }
+    kset K;
+    if (kset_build(box, kmax, &K)) { free(t); return -1; }
+    double V = box[0] * box[1] * box[2];
+    double ef = 0.0, wf[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp parallel
+    {
+        double le = 0.0, lw[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp for schedule(dynamic, 4)
+        for (int c = 0; c < K.ncol; ++c) {
+            double kx = 2.0 * M_PI * K.col_mx[c] / box[0];
+            double ky = 2.0 * M_PI * K.col_my[c] / box[1];
+            for (int l = 0; l < K.col_len[c]; ++l) {
+                double kz = 2.0 * M_PI * (K.col_mz0[c] + l) / box[2];
+                double sr = 0.0, si = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    double th = kx * pos[3 * j] + ky * pos[3 * j + 1] + kz * pos[3 * j + 2];
+                    sr += q[j] * cos(th);
+                    si += q[j] * sin(th);
+                }
+                double S2 = sr * sr + si * si;
+                double kk = sqrt(kx * kx + ky * ky + kz * kz);
+                le += far_Fhat(t, kk, n_terms) * S2;
+                double u = far_Fhat_s2(t, kk, n_terms) * S2;
+                lw[0] += u * kx * kx; lw[1] += u * ky * ky; lw[2] += u * kz * kz;
+                lw[3] += u * kx * ky; lw[4] += u * kx * kz; lw[5] += u * ky * kz;
+            }
+        }
+#pragma omp critical
+        {
+            ef += le;
+            for (int c = 0; c < 6; ++c) wf[c] += lw[c];
+        }
+    }
+    kset_free(&K);
+    ef /= V;                              /* half space: (1/2V) sum_all = (1/V) sum_half */
+    for (int c = 0; c < 6; ++c) wf[c] = -wf[c] / V;
+    wf[0] += ef; wf[1] += ef; wf[2] += ef;
+    const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+    for (int e = 0; e < 9; ++e) {
+        if (W_near) W_near[e] = wn[map[e]];
+        if (W_far) W_far[e] = wf[map[e]];
+    }
+    free(t);
+    return 0;
+}
+
+/*
+ * Far-part virial as a real-space image sum of the first n_terms Gaussians:
+ * W = 1/2 sum_{i, j, images} q_i q_j h(|d|) d (x) d, h = sum_j a_j e^{-d^2/2 s_j^2} / s_j^2.
+ * For a neutral system this is the Poisson-summation partner of or_virial's far
+ * part (the k = 0 term is zero).  Tiny systems only.
+ */
+int or_far_virial_realspace(double b, double r0, double w0, double s0, double r_c, const double* box,
+                            int n_terms, int n, const double* pos, const double* q, double* W_far)
+{
+    or_terms* t = (or_terms*)malloc(sizeof(or_terms));
+    if (!t) return -1;
+    build_terms(b, r0, w0, s0, r_c, t);
+    int nterm = (n_terms > 0 && n_terms < t->n) ? n_terms : t->n;
+    double smax = 0.0;
+    for (int j = 0; j < nterm; ++j) if (t->s[j] > smax) smax = t->s[j];
+    int M[3];
+    for (int a = 0; a < 3; ++a) M[a] = (int)ceil(10.0 * smax / box[a]) + 1;
+    double wf[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp parallel
+    {
+        double loc[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double dx0 = pos[3 * i] - pos[3 * j];
+                double dy0 = pos[3 * i + 1] - pos[3 * j + 1];
+                double dz0 = pos[3 * i + 2] - pos[3 * j + 2];
+                for (int mx = -M[0]; mx <= M[0]; ++mx)
+                    for (int my = -M[1]; my <= M[1]; ++my)
+                        for (int mz = -M[2]; mz <= M[2]; ++mz) {
+                            double dx = dx0 + mx * box[0], dy = dy0 + my * box[1], dz = dz0 + mz * box[2];
+                            double r2 = dx * dx + dy * dy + dz * dz;
+                            double h = 0.0;
+                            for (int k = 0; k < nterm; ++k) {
+                                double s2 = t->s[k] * t->s[k];
+                                h += t->a[k] * exp(-r2 / (2.0 * s2)) / s2;
+                            }
+                            double g = 0.5 * q[i] * q[j] * h;
+                            loc[0] += g * dx * dx; loc[1] += g * dy * dy; loc[2] += g * dz * dz;
+                            loc[3] += g * dx * dy; loc[4] += g * dx * dz; loc[5] += g * dy * dz;
+                        }
+            }
+#pragma omp critical
+        for (int c = 0; c < 6; ++c) wf[c] += loc[c];
+    }
+    const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+    for (int e = 0; e < 9; ++e) W_far[e] = wf[map[e]];
+    free(t);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ Ewald */
 
 /*

@@ -53,6 +53,7 @@ struct usr_ctx {
     void* d_Bt_hi[3] = {nullptr, nullptr, nullptr};
     void* d_Bt_lo[3] = {nullptr, nullptr, nullptr};
     float* d_mu = nullptr;
+    double* d_ktab = nullptr;            // 1D kernels, means and scales of the plan (table-build input)
     usr::ConvTcMaps maps[3];
     usr::ConvTcArgs targs[3];
     int tbatches[3] = {0, 0, 0};
@@ -99,7 +100,7 @@ void free_all(usr_ctx* c)
                     c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_tilebuf,
                     c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_rho_hi, c->d_rho_lo, c->d_X_hi, c->d_X_lo,
                     c->d_Y_hi, c->d_Y_lo, c->d_Bt_hi[0], c->d_Bt_hi[1], c->d_Bt_hi[2], c->d_Bt_lo[0],
-                    c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean};
+                    c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_made)
@@ -134,16 +135,6 @@ size_t tab_ints(const Plan& P, int a)
     return head + P.red_pair[a].size();
 }
 
-/* Host round-to-nearest (ties away from zero) to TF32, as cvt.rna.tf32.f32 does. */
-float tf32_rna(float f)
-{
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-
 /* Tile shape of one tensor-core pass with n_out output columns and contraction K. */
 void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16)
 {
@@ -163,42 +154,6 @@ void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16)
     // keep (CTAs per SM) x (TMEM columns) <= 512 by padding the shared memory request
     const size_t floor_smem = (size_t)228 * 1024 * a.tmem_cols / 512 + 1024;
     a.smem = (int)std::max(usr::conv_tc_smem(a), floor_smem);
-}
-
-/*
- * B tables of the three tensor-core passes: rows [batch][tile][NT] of length
- * K; row c < cols of tile t is output column m = t cols + c, row cols is the
- * DC row, the rest are zero.
- */
-std::vector<double> tc_table(const Plan& P, int pass, const usr::ConvTcArgs& a, int batches)
-{
-    const int N = P.N, nz = P.n[2];
-    std::vector<double> B((size_t)batches * a.ntiles * a.NT * a.K, 0.0);
-    for (int b = 0; b < batches; ++b)
-        for (int t = 0; t < a.ntiles; ++t)
-            for (int c = 0; c <= a.cols; ++c) {
-                double* row = B.data() + (((size_t)b * a.ntiles + t) * a.NT + c) * a.K;
-                const int m = t * a.cols + c;
-                if (c == a.cols) {                  // DC row
-                    if (pass == 3) {
-                        for (int j = 0; j < N; ++j)
-                            for (int k = 0; k < nz; ++k) row[j * nz + k] = P.scale[j] * P.mu[2][j];
-                    } else {
-                        for (int k = 0; k < a.K; ++k) row[k] = 1.0;
-                    }
-                    continue;
-                }
-                if (m >= a.n_out) continue;
-                if (pass == 3) {
-                    for (int j = 0; j < N; ++j)
-                        for (int k = 0; k < nz; ++k)
-                            row[j * nz + k] = P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz];
-                } else {
-                    const int ax = pass - 1, n = P.n[ax];
-                    for (int k = 0; k < n; ++k) row[k] = P.ktil[ax][b][((m - k) % n + n) % n];
-                }
-            }
-    return B;
 }
 
 /* Grow a device buffer to at least `bytes` (contents are not kept; growing synchronises). */
@@ -249,7 +204,9 @@ double usr::plan_device_bytes(const Plan& P)
     const double nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const double nsb = tile_blocks(P.tile);
     const double ncl = std::floor((na + 7 * ncell + 7) / 8);
-    double b = 4 * ncell * 3 + 16 * ncl * 8 + 4 * ncl * 8 + 4 * ncl + 32 * ncl;   // cells, clusters
+    const double nmax = std::max(nx, std::max(ny, nz));
+    double b = 4096 + 4 * (ncell + 1) * 3 + 16 * ncl * 8 + 4 * ncl * 8 + 4 * ncl + 32 * ncl;   // cells, clusters
+    b += 8 * (3 * N * nmax + 4 * N);                                               // 1D kernel tables
     b += na * (4 * 4 + 16 * 7);                                                    // per-atom arrays
     b += 4 * G + 8 * nsb * 5 + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
@@ -278,12 +235,11 @@ namespace {
  * enough are reused, so reconfiguring among systems of similar size allocates
  * nothing and does not synchronise the device.
  */
-usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
+usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
 {
-    Plan np;
-    usr_status s = usr::make_plan(p, &np);
-    if (s != USR_OK) return s;
+    usr_status s = USR_OK;
     c->plan = np;
+    const usr_params* p = &c->plan.p;
     const Plan& P = c->plan;
     c->max_atoms = p->max_atoms;
     c->ncell = P.cells[0] * P.cells[1] * P.cells[2];
@@ -340,30 +296,30 @@ usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
         ENSURE(c->d_wx, fl * N * nx);
         ENSURE(c->d_wy, fl * N * ny);
         ENSURE(c->d_wz, fl * N * nz);
-        std::vector<float> Bx((size_t)nx * N * nx), Ay((size_t)N * ny * ny), Az((size_t)nz * N * nz);
-        std::vector<float> wx(N * nx), wy(N * ny), wz(N * nz);
-        for (size_t j = 0; j < N; ++j) {
-            for (int k = 0; k < nx; ++k)
-                for (int m = 0; m < nx; ++m)
-                    Bx[(size_t)k * N * nx + j * nx + m] = (float)P.ktil[0][j][((m - k) % nx + nx) % nx];
-            for (int m = 0; m < ny; ++m)
-                for (int k = 0; k < ny; ++k)
-                    Ay[((size_t)j * ny + m) * ny + k] = (float)P.ktil[1][j][((m - k) % ny + ny) % ny];
-            for (int m = 0; m < nz; ++m)
-                for (int k = 0; k < nz; ++k)
-                    Az[(size_t)m * N * nz + j * nz + k] =
-                        (float)(P.scale[j] * P.ktil[2][j][((m - k) % nz + nz) % nz]);
-            for (int m = 0; m < nx; ++m) wx[j * nx + m] = (float)P.mu[0][j];
-            for (int k = 0; k < ny; ++k) wy[j * ny + k] = (float)P.mu[1][j];
-            for (int k = 0; k < nz; ++k) wz[j * nz + k] = (float)(P.scale[j] * P.mu[2][j]);
-        }
-        up.add(c->d_Bx, Bx.data(), Bx.size());
-        up.add(c->d_Ay, Ay.data(), Ay.size());
-        up.add(c->d_Az, Az.data(), Az.size());
-        up.add(c->d_wx, wx.data(), wx.size());
-        up.add(c->d_wy, wy.data(), wy.size());
-        up.add(c->d_wz, wz.data(), wz.size());
     }
+    // 1D kernels of the plan: [3][N][nmax] values, then [3][N] means, then [N] scales
+    const int nmax = std::max(nx, std::max(ny, nz));
+    const size_t nkt = 3 * N * (size_t)nmax + 3 * N + N;
+    ENSURE(c->d_ktab, db * nkt);
+    {
+        std::vector<double> kt(nkt, 0.0);
+        for (int a = 0; a < 3; ++a)
+            for (size_t j = 0; j < N; ++j) {
+                std::copy(P.ktil[a][j].begin(), P.ktil[a][j].end(), kt.begin() + (a * N + j) * nmax);
+                kt[3 * N * nmax + a * N + j] = P.mu[a][j];
+            }
+        for (size_t j = 0; j < N; ++j) kt[3 * N * nmax + 3 * N + j] = P.scale[j];
+        up.add(c->d_ktab, kt.data(), kt.size());
+    }
+    usr::ConvTableArgs tab{};
+    tab.N = (int)N;
+    tab.n[0] = nx;
+    tab.n[1] = ny;
+    tab.n[2] = nz;
+    tab.nmax = nmax;
+    tab.ktil = c->d_ktab;
+    tab.mu = c->d_ktab + 3 * N * nmax;
+    tab.scale = c->d_ktab + 3 * N * nmax + 3 * N;
     fill_args(c);
     // per axis: tile origins, then reduction counts, then (block, offset) pairs
     for (int a = 0; a < 3; ++a) {
@@ -405,26 +361,9 @@ usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
             usr::ConvTcArgs& a = c->targs[ps];
             std::memset(&a, 0, sizeof(a));
             tc_shape(a, n_out[ps], Ks[ps], bf);
-            std::vector<double> B = tc_table(P, ps + 1, a, batches[ps]);
-            ENSURE(c->d_Bt_hi[ps], es * B.size());
-            ENSURE(c->d_Bt_lo[ps], es * B.size());
-            if (bf) {
-                std::vector<__nv_bfloat16> h(B.size()), l(B.size());
-                for (size_t i = 0; i < B.size(); ++i) {
-                    h[i] = __float2bfloat16_rn((float)B[i]);
-                    l[i] = __float2bfloat16_rn((float)(B[i] - (double)__bfloat162float(h[i])));
-                }
-                up.add(c->d_Bt_hi[ps], h.data(), h.size());
-                up.add(c->d_Bt_lo[ps], l.data(), l.size());
-            } else {
-                std::vector<float> h(B.size()), l(B.size());
-                for (size_t i = 0; i < B.size(); ++i) {
-                    h[i] = tf32_rna((float)B[i]);
-                    l[i] = tf32_rna((float)(B[i] - (double)h[i]));
-                }
-                up.add(c->d_Bt_hi[ps], h.data(), h.size());
-                up.add(c->d_Bt_lo[ps], l.data(), l.size());
-            }
+            const size_t nB = (size_t)batches[ps] * a.ntiles * a.NT * a.K;
+            ENSURE(c->d_Bt_hi[ps], es * nB);
+            ENSURE(c->d_Bt_lo[ps], es * nB);
         }
         void* a_hi[3] = {c->d_rho_hi, c->d_X_hi, c->d_Y_hi};
         void* a_lo[3] = {c->d_rho_lo, c->d_X_lo, c->d_Y_lo};
@@ -477,7 +416,24 @@ usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
     if (!c->stage_ev && cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess)
         return USR_ERR_CUDA;
     if (cudaEventRecord(c->stage_ev, st) != cudaSuccess) return USR_ERR_CUDA;
-    return USR_OK;
+    // convolution tables, built on the device from the uploaded kernels
+    if (c->tc) {
+        const int batches[3] = {(int)N, (int)N, 1};
+        for (int ps = 0; ps < 3; ++ps)
+            usr::launch_tc_table(c->tc_bf16, tab, ps + 1, batches[ps], c->targs[ps], c->d_Bt_hi[ps], c->d_Bt_lo[ps],
+                                 st);
+    } else {
+        usr::launch_fp32_tables(tab, c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz, st);
+    }
+    return check_launch();
+}
+
+usr_status configure(usr_ctx* c, const usr_params* p, cudaStream_t st)
+{
+    Plan np;
+    usr_status s = usr::make_plan(p, &np);
+    if (s != USR_OK) return s;
+    return configure_plan(c, np, st);
 }
 
 void fill_args(usr_ctx* c)
@@ -649,6 +605,16 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(USR_ERR_CUDA);
     *out = c;
     return USR_OK;
+}
+
+usr_status usr::reconfigure_with_plan(usr_ctx* c, const Plan& P, cudaStream_t st)
+{
+    if (!c) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    c->parts_valid = false;
+    c->prof_valid = false;
+    return configure_plan(c, P, st);
 }
 
 extern "C" usr_status usr_reconfigure(usr_ctx* c, const usr_params* p, void* stream)

@@ -81,6 +81,9 @@ usr_status make_plan(const usr_params* p, Plan* out);
 /* Device bytes a context holds for a plan (the buffers of usr_api.cu's configure). */
 double plan_device_bytes(const Plan& P);
 
+/* usr_reconfigure with a plan already made (the serving loop plans once per request). */
+usr_status reconfigure_with_plan(usr_ctx* c, const Plan& P, cudaStream_t st);
+
 /* Canonical single-precision box constants per axis (see the oracle's predicate). */
 struct BoxF {
     float L[3];       // (float)L
@@ -147,6 +150,14 @@ struct ConvTcArgs {
     void* out_lo;           // pass output (lo part; unused for pass 3)
     int* status;
 };
+/* Inputs of the device-side table build (k_tables.cu). */
+struct ConvTableArgs {
+    int N, n[3], nmax;
+    const double* ktil;     // [3][N][nmax]: zero-mean periodised kernel of term j on axis a
+    const double* mu;       // [3][N]: its mean
+    const double* scale;    // [N]: term scale (folded into the z tables)
+};
+
 struct ConvTcMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
@@ -166,6 +177,10 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
                    void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
                    cudaStream_t st);
 void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
+void launch_fp32_tables(const ConvTableArgs& t, float* Bx, float* Ay, float* Az, float* wx, float* wy, float* wz,
+                        cudaStream_t st);
+void launch_tc_table(bool bf16, const ConvTableArgs& t, int pass, int batches, const ConvTcArgs& a, void* hi,
+                     void* lo, cudaStream_t st);
 usr_status make_tmap(CUtensorMap* m, const void* ptr, bool bf16, long long rows, int K, int box_rows);
 size_t conv_tc_smem(const ConvTcArgs& g);
 usr_status conv_tc_setup(bool bf16, size_t smem);

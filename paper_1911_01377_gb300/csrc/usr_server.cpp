@@ -23,6 +23,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -37,6 +38,8 @@ using Clock = std::chrono::steady_clock;
 struct Request {
     long long ticket;
     usr_params params;
+    std::shared_ptr<usr::Plan> plan;     // made by the worker at admission
+    double need = 0.0;                   // device bytes of a fresh context for it
     int n;
     const float* xyzq;
     float* out;
@@ -86,7 +89,7 @@ usr_status launch(usr_server* s, Slot& sl, const Request& r)
     usr_status st;
     if (!sl.ctx) {
         if ((st = usr_init(&r.params, &sl.ctx)) != USR_OK) return st;
-    } else if ((st = usr_reconfigure(sl.ctx, &r.params, sl.st)) != USR_OK) {
+    } else if ((st = usr::reconfigure_with_plan(sl.ctx, *r.plan, sl.st)) != USR_OK) {
         return st;
     }
     usr_plan_info info;
@@ -100,11 +103,24 @@ usr_status launch(usr_server* s, Slot& sl, const Request& r)
     return USR_OK;
 }
 
-double plan_bytes(const usr_params& p)
+/* Plan a queued request once (the worker keeps the plan with the request). */
+void plan_request(Request& r)
 {
-    usr_plan_info info;
-    if (usr_plan(&p, &info) != USR_OK) return -1.0;
-    return info.device_bytes;
+    if (r.plan) return;
+    r.plan = std::make_shared<usr::Plan>();
+    r.need = usr::make_plan(&r.params, r.plan.get()) == USR_OK ? usr::plan_device_bytes(*r.plan) : -1.0;
+}
+
+/* Free the contexts of idle slots (all but `keep`): the only way held memory shrinks. */
+void release_idle(usr_server* s, int keep)
+{
+    for (size_t i = 0; i < s->slots.size(); ++i) {
+        Slot& sl = s->slots[i];
+        if ((int)i == keep || sl.busy || !sl.ctx) continue;
+        usr_destroy(sl.ctx);
+        sl.ctx = nullptr;
+        sl.bytes = 0.0;
+    }
 }
 
 void worker_loop(usr_server* s)
@@ -134,25 +150,44 @@ void worker_loop(usr_server* s)
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 if (s->queue.empty()) break;
+                if (s->stop) {                                     // shutting down: cancel what waits
+                    for (const auto& q : s->queue) s->done.push_back({q.ticket, 0.0, USR_ERR_ARG});
+                    s->completed += (long long)s->queue.size();
+                    s->queue.clear();
+                    s->cv.notify_all();
+                    break;
+                }
+                plan_request(s->queue.front());
                 r = s->queue.front();
             }
-            const double need = plan_bytes(r.params);
-            // the free slot that needs the least new memory
+            const double need = r.need;
+            // a free slot, preferring the one holding the most (its buffers are the likeliest to fit)
             int best = -1;
-            double best_growth = 0.0;
             for (size_t i = 0; i < s->slots.size(); ++i) {
                 const Slot& sl = s->slots[i];
                 if (sl.busy) continue;
-                const double growth = std::max(0.0, need - sl.bytes);
-                if (best < 0 || growth < best_growth) {
-                    best = (int)i;
-                    best_growth = growth;
-                }
+                if (best < 0 || sl.bytes > s->slots[best].bytes) best = (int)i;
             }
             if (best < 0) break;                                   // no free slot
+            // a slot re-targeted to the request holds at most its current bytes plus the request's
+            // own need (buffers grow to the larger of the two), so admit only if that fits
             double held = 0.0;
-            for (const auto& sl : s->slots) held += sl.bytes;
-            if (need < 0.0 || need > budget || (held + best_growth > budget && best_growth > 0.0)) {
+            bool any_busy = false;
+            for (const auto& sl : s->slots) {
+                held += sl.bytes;
+                any_busy = any_busy || sl.busy;
+            }
+            double best_growth = need;
+            if (need >= 0.0 && need <= budget && held + best_growth > budget && !any_busy) {
+                // nothing runs, so waiting frees nothing: release idle slots, then if needed the chosen one
+                release_idle(s, best);
+                held = s->slots[best].bytes;
+                if (held + best_growth > budget) {
+                    release_idle(s, -1);
+                    held = 0.0;
+                }
+            }
+            if (need < 0.0 || need > budget || held + best_growth > budget) {
                 if (need >= 0.0 && need <= budget) break;          // wait for memory
                 std::lock_guard<std::mutex> lk(s->mu);             // can never fit: fail it
                 s->queue.pop_front();
