@@ -100,6 +100,8 @@ typedef struct {
     int spread_points;           /* spreading stencil points per axis (even, 8..16); 0 = 12 */
     usr_conv conv;
     int max_atoms;               /* capacity of the context (rows per evaluation) */
+    int virial;                  /* 1: also compute the virial tensor (usr_virial); six more far-part
+                                    convolution sets per evaluation */
 } usr_params;
 
 /* Quantities derived from usr_params (all host-side, FP64). */
@@ -299,6 +301,21 @@ usr_status usr_debug_pairs(usr_ctx* ctx, int n, const float* xyzq, int* count, u
  */
 usr_status usr_cells_static(int n, const float* xyzq, const double* box, const int* cells, int* cell, int* perm,
                             int* cell_start, float* xw, void* stream);
+
+/*
+ * Virial tensor of the last usr_eval of a context created with virial = 1:
+ * W = -dE/d(strain) for an affine strain of the box and all positions,
+ * row-major 3 x 3 doubles (symmetric), W = W_near + W_far:
+ *   W_near = 1/2 sum_{i != j, images, r < r_c} d (x) f_ij    (pair forces of Eq. 20)
+ *   W_far_ab = delta_ab E_far - (1/2V) sum_{k != 0} |S(k)|^2 k_a k_b sum_j s_j^2 Fhat_j(k)
+ * (the strain derivative of the far energy of Eqs. 4, 9 and F1; the self term of Eq. 10 has
+ * none).  The far part is evaluated on the grid: every strain derivative of a Gaussian stays
+ * separable (Eq. 31), so W_far_ab - delta_ab E_far = 1/2 <rho, psi_ab> with psi_ab the
+ * convolution of rho with s_j^2 d_a d_b of each term's deconvolved kernel.  W is written to
+ * `W` (device or host memory, 9 doubles) on `stream`; USR_ERR_ARG without virial = 1 or
+ * before any evaluation.
+ */
+usr_status usr_virial(usr_ctx* ctx, double* W, void* stream);
 
 /* Keep (on != 0) or stop keeping the near and far parts of each usr_eval. */
 usr_status usr_set_keep_parts(usr_ctx* ctx, int on);

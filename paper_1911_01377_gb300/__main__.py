@@ -21,6 +21,10 @@ def main(argv=None):
     ap.add_argument("--rc", type=float, default=0.0, help="cutoff (default: the workload's first)")
     ap.add_argument("--series", default="C1_B2", choices=sorted(usr.PRESETS))
     ap.add_argument("--evals", type=int, default=1)
+    ap.add_argument("--conv", type=int, default=0, choices=[0, 1, 2], help="0 FP32, 1 TF32x3, 2 BF16x3")
+    ap.add_argument("--spread-points", type=int, default=0)
+    ap.add_argument("--spread-sigma", type=float, default=0.0, help="spreading width / grid spacing")
+    ap.add_argument("--virial", type=int, default=0, choices=[0, 1])
     args = ap.parse_args(argv)
 
     import torch
@@ -28,7 +32,8 @@ def main(argv=None):
     B.build()
     w = W.get(args.workload)
     r_c = args.rc or w.r_c[0]
-    ctx = usr.USeries(w.box, w.grid, r_c, args.series, max_atoms=w.n)
+    ctx = usr.USeries(w.box, w.grid, r_c, args.series, max_atoms=w.n, conv=args.conv,
+                      spread_points=args.spread_points, spread_sigma_over_h=args.spread_sigma, virial=args.virial)
     usr.usr_set_profiling(ctx.ctx, True)
     x = torch.from_numpy(w.xyzq).cuda()
     out = torch.empty((w.n, 4), dtype=torch.float32, device="cuda")
@@ -43,6 +48,8 @@ def main(argv=None):
     info = ctx.info
     print(f"{w.name}: n={w.n} r_c={r_c:g} grid={w.grid} terms={info.n_terms} cells={tuple(info.cells)}")
     print(f"E={e[0]:.10f} E_near={e[1]:.10f} E_far={e[2]:.10f} E_self={e[3]:.10f}")
+    if args.virial:
+        print("virial:", ctx.virial().cpu().numpy().round(6).tolist())
     ms = usr.usr_stage_times(ctx.ctx)
     print("stage ms: " + " ".join(f"{k}={v:.4f}" for k, v in zip(usr.STAGES, ms)) + f" total={sum(ms):.4f}")
     ctx.close()

@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(const int* __restric
  * are ordered by the Morton code of their position on an 8 x 8 x 8 lattice
  * inside the cell (ties by sorted index), so that runs of 8 are compact;
  * written to the padded layout at pstart[c] with dummy rows (q = 0, far
- * away, index -1) after the last atom; then each cluster's bounding box.
+ * away and far apart, index -1) after the last atom; then each cluster's
+ * bounding box.
  */
 __device__ __forceinline__ int spread3(int v)
 {
@@ -193,7 +194,9 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
         cidx[p0 + r] = s0 + e;
     }
     for (int e = m + threadIdx.x; e < pm; e += kSortThreads) {
-        cpos[p0 + e] = make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.0f);
+        // padding rows: far from the box and 4e4 A apart, so no pair involving one is ever within r_c
+        const float far = -1.0e6f - 4.0e4f * (float)(e & 7);
+        cpos[p0 + e] = make_float4(far, far, far, 0.0f);
         cidx[p0 + e] = -1;
     }
     __syncthreads();

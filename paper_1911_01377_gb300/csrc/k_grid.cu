@@ -32,7 +32,7 @@ namespace usr {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;          // 16 warps: one CTA per block of cells keeps the halo small, so each CTA carries many warps
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;         // atoms whose weights are staged at once (spread)
 constexpr int kGChunk = 128;        // atoms staged at once (gather)
@@ -120,7 +120,7 @@ __device__ __forceinline__ int block_atom(int j, const int* rs, const int* pre)
 /* ------------------------------------------------------------------ spread */
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 1) k_spread(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start, GridArgs g,
                                                         float* __restrict__ tilebuf, double* __restrict__ partial,
                                                         unsigned int* __restrict__ counter,
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
 template <int SPLIT>
 __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __restrict__ tilebuf,
                                                      const double* __restrict__ mean, void* __restrict__ rho,
-                                                     void* __restrict__ rho_lo)
+                                                     void* __restrict__ rho_lo, float* __restrict__ rho32)
 {
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
     const long long G = (long long)n0 * n1 * n2;
@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
         }
     }
     const float v = (float)((double)s - *mean);
+    if (SPLIT != 0 && rho32) rho32[idx] = v;     // FP32 copy for the virial convolutions
     if (SPLIT == 0) {
         static_cast<float*>(rho)[idx] = v;
     } else if (SPLIT == 1) {
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
  * Fixed-order FP64 partial sums, the last CTA finishes.
  */
 __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __restrict__ psi,
+                                                   const float* __restrict__ w, double scale,
                                                    double* __restrict__ partial, unsigned int* __restrict__ counter,
                                                    double* __restrict__ mean)
 {
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
-        s += (double)psi[i];
+        s += w ? (double)psi[i] * (double)w[i] : (double)psi[i];
     s = warp_sum_d(s);
     if (lane == 0) red[warp] = s;
     __syncthreads();
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __r
         if (threadIdx.x == 0) {
             double u = 0.0;
             for (int w = 0; w < 8; ++w) u += red[w];
-            *mean = u / (double)G;
+            *mean = u * scale;
             *counter = 0u;
         }
     }
@@ -349,13 +351,45 @@ void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsi
                       cudaStream_t st)
 {
     const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
-    k_grid_mean<<<kGridMeanBlocks, 256, 0, st>>>(G, psi, partial, counter, mean);
+    k_grid_mean<<<kGridMeanBlocks, 256, 0, st>>>(G, psi, nullptr, 1.0 / (double)G, partial, counter, mean);
+}
+
+/* out = scale * sum_g a_g b_g in FP64, fixed order (the virial's grid dot products). */
+void launch_grid_dot(const GridArgs& g, const float* a, const float* b, double scale, double* partial,
+                     unsigned int* counter, double* out, cudaStream_t st)
+{
+    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
+    k_grid_mean<<<kGridMeanBlocks, 256, 0, st>>>(G, a, b, scale, partial, counter, out);
+}
+
+/*
+ * W = W_near + delta E_far + 1/2 <rho, psi_ab>: near from per-warp slots (in
+ * warp order), far from the six grid dot products (already halved) and E_far.
+ */
+__global__ void k_virial_finalize(const double* __restrict__ near_w, int nwarps, const double* __restrict__ dots,
+                                  const double* __restrict__ energy, double* __restrict__ W)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double wn[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < nwarps; ++w)
+        for (int c = 0; c < 6; ++c) wn[c] += near_w[6 * w + c];
+    const double ef = energy[2];
+    double t[6];
+    for (int c = 0; c < 6; ++c) t[c] = wn[c] + dots[c] + (c < 3 ? ef : 0.0);
+    const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+    for (int e = 0; e < 9; ++e) W[e] = t[map[e]];
+}
+
+void launch_virial_finalize(const double* near_w, int nwarps, const double* dots, const double* energy, double* W,
+                            cudaStream_t st)
+{
+    k_virial_finalize<<<1, 32, 0, st>>>(near_w, nwarps, dots, energy, W);
 }
 
 /* ------------------------------------------------------------------ gather */
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 1) k_gather(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start,
                                                         const int* __restrict__ perm,
                                                         const float4* __restrict__ near_out,
@@ -583,7 +617,7 @@ usr_status grid_kernel_setup(size_t bytes)
 
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
                    void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
-                   cudaStream_t st)
+                   cudaStream_t st, float* rho32)
 {
     const int nb = tile_blocks(g.tg);
     const size_t smem = sizeof(float) * tile_floats(g.tg);
@@ -598,11 +632,11 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
     const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
     const unsigned nr = (unsigned)((G + 255) / 256);
     if (split == 1)
-        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo);
+        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32);
     else if (split == 2)
-        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo);
+        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32);
     else
-        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr);
+        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr);
 }
 
 #define USR_GATHER_CASE(PP)                                                                                      \

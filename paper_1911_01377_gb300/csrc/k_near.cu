@@ -31,19 +31,29 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
     return z ^ (z >> 31);
 }
 
-/* COUNT = true: instead of the interaction, count partners and hash their caller indices. */
-template <int DEG, bool COUNT>
+/*
+ * COUNT = true: instead of the interaction, count partners and hash their caller indices.
+ * VIR = true: also accumulate the pair virial 1/2 sum d (x) f (six components, FP32 per lane,
+ * summed over the warp in a fixed order and written as FP64 to vir[6 * warp ..], one slot per
+ * warp of the grid).
+ */
+template <int DEG, bool COUNT, bool VIR>
 __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos, const int* __restrict__ cidx,
                                                  const int* __restrict__ ccell, const float4* __restrict__ bblo,
                                                  const float4* __restrict__ bbhi, const int* __restrict__ pstart,
                                                  const int* __restrict__ perm, NearArgs a, float4* __restrict__ out,
-                                                 int* __restrict__ count, unsigned long long* __restrict__ hash)
+                                                 int* __restrict__ count, unsigned long long* __restrict__ hash,
+                                                 double* __restrict__ vir)
 {
     const int ncx = a.box.nc[0], ncy = a.box.nc[1], ncz = a.box.nc[2];
     const int ncl = pstart[ncx * ncy * ncz] >> 3;
     const int ic = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (ic >= ncl) return;
     const int lane = threadIdx.x & 31;
+    float vxx = 0.f, vyy = 0.f, vzz = 0.f, vxy = 0.f, vxz = 0.f, vyz = 0.f;
+    if (ic >= ncl) {
+        if (VIR && lane < 6) vir[6 * ic + lane] = 0.0;    // one slot per warp, idle warps write zeros
+        return;
+    }
     const int il = lane >> 2, jl = lane & 3;
     const int islot = ic * 8 + il;
     const float4 pi = cpos[islot];
@@ -114,6 +124,14 @@ __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos
                         fx = fmaf(gsc, dx, fx);
                         fy = fmaf(gsc, dy, fy);
                         fz = fmaf(gsc, dz, fz);
+                        if (VIR) {
+                            vxx = fmaf(gsc * dx, dx, vxx);
+                            vyy = fmaf(gsc * dy, dy, vyy);
+                            vzz = fmaf(gsc * dz, dz, vzz);
+                            vxy = fmaf(gsc * dx, dy, vxy);
+                            vxz = fmaf(gsc * dx, dz, vxz);
+                            vyz = fmaf(gsc * dy, dz, vyz);
+                        }
                     }
                 }
             }
@@ -139,29 +157,49 @@ __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos
             out[si] = make_float4(pi.w * fx, pi.w * fy, pi.w * fz, ph);
         }
     }
+    if (VIR) {
+        // 1/2 q_i sum_j gsc d (x) d, summed over the warp (fixed tree), then over the CTA
+        const double hq = si >= 0 ? 0.5 * (double)pi.w : 0.0;    // padding rows contribute nothing
+        double v[6] = {hq * vxx, hq * vyy, hq * vzz, hq * vxy, hq * vxz, hq * vyz};
+        if (si < 0)
+            for (int c = 0; c < 6; ++c) v[c] = 0.0;
+        #pragma unroll
+        for (int c = 0; c < 6; ++c)
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+        if (lane == 0)
+            for (int c = 0; c < 6; ++c) vir[6 * ic + c] = v[c];
+    }
 }
 
 template <int DEG, bool COUNT>
 static void launch_cl(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
                       const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, float4* out,
-                      int* count, unsigned long long* hash, cudaStream_t st)
+                      int* count, unsigned long long* hash, cudaStream_t st, double* vir = nullptr)
 {
     const int blocks = (max_clusters + 3) / 4;
-    k_near_cl<DEG, COUNT><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out, count, hash);
+    if (vir)
+        k_near_cl<DEG, COUNT, true><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out, count,
+                                                             hash, vir);
+    else
+        k_near_cl<DEG, COUNT, false><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out,
+                                                              count, hash, nullptr);
 }
 
+int near_warps(int max_clusters) { return 4 * ((max_clusters + 3) / 4); }
+
 void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
-                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st)
+                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st, double* vir)
 {
     switch (deg) {
-        case 6: launch_cl<6, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 7: launch_cl<7, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 8: launch_cl<8, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 10: launch_cl<10, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 12: launch_cl<12, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 16: launch_cl<16, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        case 20: launch_cl<20, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
-        default: launch_cl<24, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st); break;
+        case 6: launch_cl<6, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 7: launch_cl<7, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 8: launch_cl<8, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 10: launch_cl<10, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 12: launch_cl<12, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 16: launch_cl<16, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 20: launch_cl<20, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        default: launch_cl<24, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
     }
 }
 

@@ -54,6 +54,13 @@ struct usr_ctx {
     void* d_Bt_lo[3] = {nullptr, nullptr, nullptr};
     float* d_mu = nullptr;
     double* d_ktab = nullptr;            // 1D kernels, means and scales of the plan (table-build input)
+    // virial: per strain component (xx yy zz xy xz yz) FP32 tables {Bx, Ay, Az, wx, wy, wz} and their input
+    bool vir = false;
+    float* d_vtab[6][6] = {};
+    double* d_vktab = nullptr;
+    float *d_psiv = nullptr, *d_rho32 = nullptr;
+    double *d_vnear = nullptr, *d_vdot = nullptr, *d_vpart = nullptr, *d_W = nullptr;
+    bool vir_valid = false;
     usr::ConvTcMaps maps[3];
     usr::ConvTcArgs targs[3];
     int tbatches[3] = {0, 0, 0};
@@ -103,6 +110,12 @@ void free_all(usr_ctx* c)
                     c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    void* vptrs[] = {c->d_vktab, c->d_psiv, c->d_rho32, c->d_vnear, c->d_vdot, c->d_vpart, c->d_W};
+    for (void* p : vptrs)
+        if (p) cudaFree(p);
+    for (auto& comp : c->d_vtab)
+        for (float* p : comp)
+            if (p) cudaFree(p);
     if (c->ev_made)
         for (auto& e : c->ev) cudaEventDestroy(e);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -210,6 +223,11 @@ double usr::plan_device_bytes(const Plan& P)
     b += na * (4 * 4 + 16 * 7);                                                    // per-atom arrays
     b += 4 * G + 8 * nsb * 5 + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
+    if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
+        b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
+        b += 8 * G + 48 * 4 * std::ceil((na + 7 * ncell + 7) / 32) + 8 * (16 + kGridMeanBlocks);
+        if (tc) b += 4 * G * (1 + 2 * N);
+    }
     if (!tc) {
         b += 4 * G * (1 + 2 * N) + 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz);
     } else {
@@ -276,7 +294,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_mean, db);
     ENSURE(c->d_gather_partial, db * nsb * 4);
     ENSURE(c->d_energy, db * 4);
-    ENSURE(c->d_counters, sizeof(unsigned int) * 3);
+    ENSURE(c->d_counters, sizeof(unsigned int) * 4);
     ENSURE(c->d_psi_partial, db * usr::kGridMeanBlocks);
     ENSURE(c->d_psi_mean, db);
     ENSURE(c->d_in, f4 * na);
@@ -286,7 +304,9 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_tilebuf, fl * nsb * usr::tile_floats(P.tile));
     for (int a = 0; a < 3; ++a) ENSURE(c->d_tab[a], i4 * tab_ints(P, a));
     Staged up;
-    if (!c->tc) {
+    c->vir = p->virial != 0;
+    c->vir_valid = false;
+    if (!c->tc || c->vir) {
         ENSURE(c->d_rho, fl * G);
         ENSURE(c->d_X, fl * N * G);
         ENSURE(c->d_Y, fl * N * G);
@@ -310,6 +330,50 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
             }
         for (size_t j = 0; j < N; ++j) kt[3 * N * nmax + 3 * N + j] = P.scale[j];
         up.add(c->d_ktab, kt.data(), kt.size());
+    }
+    // virial: per strain component, the 1D kernels with the derivative order of each axis and the
+    // term weight scale_j s_j^2 (the s_j^2 d_a d_b of each term's kernel, Eq. 31 separability)
+    static const int kVirOrder[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    usr::ConvTableArgs vtab[6];
+    if (c->vir) {
+        ENSURE(c->d_vktab, db * nkt * 6);
+        ENSURE(c->d_psiv, fl * G);
+        if (c->tc) ENSURE(c->d_rho32, fl * G);
+        ENSURE(c->d_vnear, db * 6 * usr::near_warps(c->max_clusters));
+        ENSURE(c->d_vdot, db * 6);
+        ENSURE(c->d_vpart, db * usr::kGridMeanBlocks);
+        ENSURE(c->d_W, db * 9);
+        for (int cmp = 0; cmp < 6; ++cmp) {
+            ENSURE(c->d_vtab[cmp][0], fl * nx * N * nx);
+            ENSURE(c->d_vtab[cmp][1], fl * N * ny * ny);
+            ENSURE(c->d_vtab[cmp][2], fl * nz * N * nz);
+            ENSURE(c->d_vtab[cmp][3], fl * N * nx);
+            ENSURE(c->d_vtab[cmp][4], fl * N * ny);
+            ENSURE(c->d_vtab[cmp][5], fl * N * nz);
+        }
+        std::vector<double> kt(nkt * 6, 0.0);
+        for (int cmp = 0; cmp < 6; ++cmp) {
+            double* base = kt.data() + nkt * cmp;
+            for (int a = 0; a < 3; ++a) {
+                const int o = kVirOrder[cmp][a];
+                for (size_t j = 0; j < N; ++j) {
+                    const std::vector<double>& src = o == 0 ? P.ktil[a][j] : P.ktil_d[o - 1][a][j];
+                    std::copy(src.begin(), src.end(), base + (a * N + j) * nmax);
+                    base[3 * N * nmax + a * N + j] = o == 0 ? P.mu[a][j] : P.mu_d[o - 1][a][j];
+                }
+            }
+            for (size_t j = 0; j < N; ++j) base[3 * N * nmax + 3 * N + j] = P.scale[j] * P.s[j] * P.s[j];
+            usr::ConvTableArgs& t = vtab[cmp];
+            t.N = (int)N;
+            t.n[0] = nx;
+            t.n[1] = ny;
+            t.n[2] = nz;
+            t.nmax = nmax;
+            t.ktil = c->d_vktab + nkt * cmp;
+            t.mu = t.ktil + 3 * N * nmax;
+            t.scale = t.ktil + 3 * N * nmax + 3 * N;
+        }
+        up.add(c->d_vktab, kt.data(), kt.size());
     }
     usr::ConvTableArgs tab{};
     tab.N = (int)N;
@@ -425,6 +489,10 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     } else {
         usr::launch_fp32_tables(tab, c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz, st);
     }
+    if (c->vir)
+        for (int cmp = 0; cmp < 6; ++cmp)
+            usr::launch_fp32_tables(vtab[cmp], c->d_vtab[cmp][0], c->d_vtab[cmp][1], c->d_vtab[cmp][2],
+                                    c->d_vtab[cmp][3], c->d_vtab[cmp][4], c->d_vtab[cmp][5], st);
     return check_launch();
 }
 
@@ -481,6 +549,53 @@ void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
 }
 
 /* The evaluation sequence; xyzq/out are device pointers already checked. */
+/*
+ * The three FP32 convolution passes of Sec. V on rho with the tables
+ * {Bx, Ay, Az, wx, wy, wz} into psi (X and Y are the context's scratch); after
+ * each pass `after(k)` is called (stage marks).
+ */
+template <typename F>
+void fp32_conv(usr_ctx* c, const float* rho, float* const* t, float* psi, cudaStream_t st, F after)
+{
+    const Plan& P = c->plan;
+    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const long long G = c->G;
+    {   // x pass: all terms
+        usr::ConvGemm g{};
+        g.M = ny * nz; g.N = N * nx; g.K = nx;
+        g.A = rho; g.lda = nx;
+        g.B = t[0]; g.ldb = (long long)N * nx;
+        g.C = c->d_X; g.ldc = nx;
+        g.nb2 = 1; g.nsplit = nx; g.c_split = G;
+        g.mode = 1; g.dcw = t[3]; g.mean = nullptr;   // rho has its mean removed already
+        usr::launch_conv(g, 1, st);
+    }
+    after(0);
+    {   // y pass: batched over (term, z)
+        usr::ConvGemm g{};
+        g.M = ny; g.N = nx; g.K = ny;
+        g.A = t[1]; g.lda = ny; g.a_s1 = (long long)ny * ny; g.a_s2 = 0;
+        g.B = c->d_X; g.ldb = nx; g.b_s1 = G; g.b_s2 = (long long)ny * nx;
+        g.C = c->d_Y; g.ldc = nx; g.c_s1 = G; g.c_s2 = (long long)ny * nx;
+        g.nb2 = nz; g.nsplit = 1 << 30; g.c_split = 0;
+        g.mode = 2; g.dcw = t[4]; g.dcw_s1 = ny;
+        usr::launch_conv(g, N * nz, st);
+    }
+    after(1);
+    {   // z pass: sum over terms folded into K
+        usr::ConvGemm g{};
+        g.M = nz; g.N = nx * ny; g.K = N * nz;
+        g.A = t[2]; g.lda = (long long)N * nz;
+        g.B = c->d_Y; g.ldb = (long long)nx * ny;
+        g.C = psi; g.ldc = (long long)nx * ny;
+        g.nb2 = 1; g.nsplit = 1 << 30; g.c_split = 0;
+        g.mode = 2; g.dcw = t[5]; g.dcw_s1 = 0;
+        usr::launch_conv(g, 1, st);
+    }
+    after(2);
+}
+
+/* The evaluation sequence; xyzq/out are device pointers already checked. */
 usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* energy, cudaStream_t st)
 {
     const Plan& P = c->plan;
@@ -489,8 +604,11 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     c->last_n = n;
     c->parts_valid = false;
     c->prof_valid = false;
+    c->vir_valid = false;
     if (n == 0) {
         if (cudaMemsetAsync(en, 0, 4 * sizeof(double), st) != cudaSuccess) return USR_ERR_CUDA;
+        if (c->vir && cudaMemsetAsync(c->d_W, 0, 9 * sizeof(double), st) != cudaSuccess) return USR_ERR_CUDA;
+        c->vir_valid = c->vir;
         return USR_OK;
     }
     auto mark = [&](int k) {
@@ -500,69 +618,48 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     bin_and_cluster(c, n, xyzq, st);
     mark(1);
     usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
-                     c->d_pstart, c->near, c->d_near, st);
+                     c->d_pstart, c->near, c->d_near, st, c->vir ? c->d_vnear : nullptr);
     mark(2);
     if (c->tc)
         usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
-                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
+                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st,
+                           c->vir ? c->d_rho32 : nullptr);
     else
         usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
                            c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
     mark(3);
-    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const long long G = c->G;
     if (c->tc) {
         for (int p = 0; p < 3; ++p) {
             usr::launch_conv_tc(c->tc_bf16, c->maps[p], c->targs[p], c->tbatches[p], st);
             mark(4 + p);
         }
     } else {
-    {   // x pass: all terms
-        usr::ConvGemm g{};
-        g.M = ny * nz; g.N = N * nx; g.K = nx;
-        g.A = c->d_rho; g.lda = nx;
-        g.B = c->d_Bx; g.ldb = (long long)N * nx;
-        g.C = c->d_X; g.ldc = nx;
-        g.nb2 = 1; g.nsplit = nx; g.c_split = G;
-        g.mode = 1; g.dcw = c->d_wx; g.mean = nullptr;   // rho has its mean removed already
-        usr::launch_conv(g, 1, st);
-    }
-    mark(4);
-    {   // y pass: batched over (term, z)
-        usr::ConvGemm g{};
-        g.M = ny; g.N = nx; g.K = ny;
-        g.A = c->d_Ay; g.lda = ny; g.a_s1 = (long long)ny * ny; g.a_s2 = 0;
-        g.B = c->d_X; g.ldb = nx; g.b_s1 = G; g.b_s2 = (long long)ny * nx;
-        g.C = c->d_Y; g.ldc = nx; g.c_s1 = G; g.c_s2 = (long long)ny * nx;
-        g.nb2 = nz; g.nsplit = 1 << 30; g.c_split = 0;
-        g.mode = 2; g.dcw = c->d_wy; g.dcw_s1 = ny;
-        usr::launch_conv(g, N * nz, st);
-    }
-    mark(5);
-    {   // z pass: sum over terms folded into K
-        usr::ConvGemm g{};
-        g.M = nz; g.N = nx * ny; g.K = N * nz;
-        g.A = c->d_Az; g.lda = (long long)N * nz;
-        g.B = c->d_Y; g.ldb = (long long)nx * ny;
-        g.C = c->d_psi; g.ldc = (long long)nx * ny;
-        g.nb2 = 1; g.nsplit = 1 << 30; g.c_split = 0;
-        g.mode = 2; g.dcw = c->d_wz; g.dcw_s1 = 0;
-        usr::launch_conv(g, 1, st);
-    }
-    mark(6);
+        float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
+        fp32_conv(c, c->d_rho, t, c->d_psi, st, [&](int k) { mark(4 + k); });
     }
     usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, st);
     usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, out,
                        c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
                        c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
     mark(7);
+    if (c->vir) {
+        // far virial: 1/2 <rho, psi_ab> per strain component, then the finalisation with E_far
+        const float* rho = c->tc ? c->d_rho32 : c->d_rho;
+        for (int cmp = 0; cmp < 6; ++cmp) {
+            fp32_conv(c, rho, c->d_vtab[cmp], c->d_psiv, st, [](int) {});
+            usr::launch_grid_dot(c->grid, rho, c->d_psiv, 0.5, c->d_vpart, c->d_counters + 3, c->d_vdot + cmp, st);
+        }
+        usr::launch_virial_finalize(c->d_vnear, usr::near_warps(c->max_clusters), c->d_vdot, en, c->d_W, st);
+    }
     usr_status s = check_launch();
     if (s == USR_OK) {
         c->parts_valid = c->keep_parts;
         c->prof_valid = c->prof;
+        c->vir_valid = c->vir;
     }
     return s;
 }
+
 
 }  // namespace
 
@@ -596,7 +693,7 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
         (s = usr::conv_tc_setup(true, usr::kConvTcMaxSmem)) != USR_OK)
         return fail(s);
     if ((s = configure(c, p, 0)) != USR_OK) return fail(s);
-    if (cudaMemset(c->d_counters, 0, 3 * sizeof(unsigned int)) != cudaSuccess ||
+    if (cudaMemset(c->d_counters, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess)
         return fail(USR_ERR_CUDA);
@@ -734,6 +831,14 @@ extern "C" usr_status usr_debug_pairs(usr_ctx* c, int n, const float* xyzq, int*
     usr::launch_pairs(c->max_clusters, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_pstart, c->d_perm,
                       c->near, count, (unsigned long long*)hash, st);
     return check_launch();
+}
+
+extern "C" usr_status usr_virial(usr_ctx* c, double* W, void* stream)
+{
+    if (!c || !W || !c->vir || !c->vir_valid) return USR_ERR_ARG;
+    if (cudaMemcpyAsync(W, c->d_W, 9 * sizeof(double), cudaMemcpyDefault, (cudaStream_t)stream) != cudaSuccess)
+        return USR_ERR_CUDA;
+    return USR_OK;
 }
 
 extern "C" usr_status usr_set_keep_parts(usr_ctx* c, int on)

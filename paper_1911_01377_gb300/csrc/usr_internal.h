@@ -68,6 +68,9 @@ struct Plan {
     std::vector<double> ktil[3][kMaxTerms];
     double mu[3][kMaxTerms];
     double scale[kMaxTerms];
+    // virial: first and second derivatives (in x) of the same periodised kernels, split the same way
+    std::vector<double> ktil_d[2][3][kMaxTerms];
+    double mu_d[2][3][kMaxTerms];
     int cells[3];
     TileGeom tile;
     std::vector<int> tile_org[3];        // per axis: tile origin of each block
@@ -169,13 +172,19 @@ void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count,
 void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
                      int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st);
 void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
-                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st);
+                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st,
+                 double* vir = nullptr);
+int near_warps(int max_clusters);
 void launch_pairs(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
                   const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, int* count,
                   unsigned long long* hash, cudaStream_t st);
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
                    void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
-                   cudaStream_t st);
+                   cudaStream_t st, float* rho32 = nullptr);
+void launch_grid_dot(const GridArgs& g, const float* a, const float* b, double scale, double* partial,
+                     unsigned int* counter, double* out, cudaStream_t st);
+void launch_virial_finalize(const double* near_w, int nwarps, const double* dots, const double* energy, double* W,
+                            cudaStream_t st);
 void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
 void launch_fp32_tables(const ConvTableArgs& t, float* Bx, float* Ay, float* Az, float* wx, float* wy, float* wz,
                         cudaStream_t st);

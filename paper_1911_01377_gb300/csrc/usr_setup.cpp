@@ -201,6 +201,51 @@ void fit_cache_put(const Plan& P, double ev)
     g_fits.push_back(f);
 }
 
+/*
+ * d^order/dx^order of the periodised kernel of periodic_kernel (order 1 or 2)
+ * at the grid points, split into mean (returned) and zero-mean part (kt).
+ * Narrow kernels: image sum of g^(order), g(y) = exp(-y^2 / (2 w^2));
+ * wide kernels: the derivative of the cosine series.
+ */
+double periodic_kernel_deriv(double w, double h, int n, int order, std::vector<double>& kt)
+{
+    double L = n * h;
+    std::vector<double> k(n, 0.0);
+    if (w < 0.25 * L) {
+        int pmax = (int)std::ceil(10.0 * w / L) + 1;
+        const double w2 = w * w;
+        for (int d = 0; d < n; ++d) {
+            double v = 0.0;
+            for (int p = -pmax; p <= pmax; ++p) {
+                double y = d * h + p * L;
+                double e = y * y / (2.0 * w2);
+                if (e >= 745.0) continue;
+                double g = std::exp(-e);
+                v += order == 1 ? -y / w2 * g : (y * y / (w2 * w2) - 1.0 / w2) * g;
+            }
+            k[d] = v;
+        }
+    } else {
+        double pref = std::sqrt(2.0 * kPi) * w / L;
+        for (int m = 1;; ++m) {
+            double km = 2.0 * kPi * m / L;
+            double e = 0.5 * w * w * km * km;
+            if (e > 745.0) break;
+            double g = 2.0 * pref * std::exp(-e);
+            for (int d = 0; d < n; ++d) {
+                double th = km * d * h;
+                k[d] += order == 1 ? -g * km * std::sin(th) : -g * km * km * std::cos(th);
+            }
+        }
+    }
+    double mean = 0.0;
+    for (int d = 0; d < n; ++d) mean += k[d];
+    mean /= n;
+    kt.assign(n, 0.0);
+    for (int d = 0; d < n; ++d) kt[d] = k[d] - mean;
+    return mean;
+}
+
 }  // namespace
 
 usr_status make_plan(const usr_params* pp, Plan* out)
@@ -220,7 +265,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
         for (int a = 0; a < 3; ++a)
             if (p.grid[a] % q != 0) return USR_ERR_BOX;
     }
-    if (p.max_atoms < 0) return USR_ERR_ARG;
+    if (p.max_atoms < 0 || (p.virial != 0 && p.virial != 1)) return USR_ERR_ARG;
     int Pst = p.spread_points ? p.spread_points : 12;
     if (Pst < 8 || Pst > 16 || (Pst & 1)) return USR_ERR_ARG;
     double ratio = p.spread_sigma_over_h > 0.0 ? p.spread_sigma_over_h : 1.0;
@@ -276,6 +321,9 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             double wc = std::sqrt(wc2);
             f *= (P.s[j] / wc) / (2.0 * kPi * P.sigma_sa[a] * P.sigma_sa[a]);
             P.mu[a][j] = periodic_kernel(wc, P.h[a], P.n[a], P.ktil[a][j]);
+            if (p.virial)
+                for (int o = 0; o < 2; ++o)
+                    P.mu_d[o][a][j] = periodic_kernel_deriv(wc, P.h[a], P.n[a], o + 1, P.ktil_d[o][a][j]);
         }
         P.scale[j] = f;
     }

@@ -29,7 +29,8 @@ class usr_series(ctypes.Structure):
 
 class usr_params(ctypes.Structure):
     _fields_ = [("box", _c_d * 3), ("grid", _c_i * 3), ("r_c", _c_d), ("series", usr_series),
-                ("spread_sigma_over_h", _c_d), ("spread_points", _c_i), ("conv", _c_i), ("max_atoms", _c_i)]
+                ("spread_sigma_over_h", _c_d), ("spread_points", _c_i), ("conv", _c_i), ("max_atoms", _c_i),
+                ("virial", _c_i)]
 
 
 class usr_plan_info(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib():
                                       ctypes.POINTER(ctypes.c_longlong)]
         L.usr_server_destroy.argtypes = [_c_p]
         L.usr_server_destroy.restype = None
+        L.usr_virial.argtypes = [_c_p, _c_p, _c_p]
         L.usr_set_keep_parts.argtypes = [_c_p, _c_i]
         L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
@@ -93,7 +95,7 @@ def lib():
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
                      "usr_eval_host",
                      "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
-                     "usr_set_keep_parts", "usr_eval_host_async", "usr_server_create", "usr_server_submit",
+                     "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_server_create", "usr_server_submit",
                      "usr_server_wait", "usr_server_info",
                      "usr_debug_parts", "usr_set_profiling", "usr_stage_times"):
             getattr(L, name).restype = _c_i
@@ -119,7 +121,7 @@ def usr_series_preset(preset) -> usr_series:
 
 
 def make_params(box, grid, r_c, series, spread_sigma_over_h=0.0, spread_points=0, conv=0, max_atoms=0,
-                n_terms=0, trunc_eps=0.0) -> usr_params:
+                n_terms=0, trunc_eps=0.0, virial=0) -> usr_params:
     if isinstance(series, (str, int)):
         series = usr_series_preset(series)
     elif not isinstance(series, usr_series):
@@ -136,6 +138,7 @@ def make_params(box, grid, r_c, series, spread_sigma_over_h=0.0, spread_points=0
     p.spread_points = int(spread_points)
     p.conv = int(conv)
     p.max_atoms = int(max_atoms)
+    p.virial = int(virial)
     return p
 
 
@@ -198,6 +201,10 @@ def usr_cells_static(n, xyzq_ptr, box, cells, cell_ptr, perm_ptr, start_ptr, xw_
     c = (_c_i * 3)(*[int(v) for v in cells])
     _check(lib().usr_cells_static(int(n), xyzq_ptr, b, c, cell_ptr, perm_ptr, start_ptr, xw_ptr,
                                   _stream_ptr(stream)), "usr_cells_static")
+
+
+def usr_virial(ctx, W_ptr, stream=None):
+    _check(lib().usr_virial(ctx, W_ptr, _stream_ptr(stream)), "usr_virial")
 
 
 def usr_set_keep_parts(ctx, on: bool):
@@ -271,6 +278,13 @@ class USeries:
             energy = torch.empty(4, dtype=torch.float64, pin_memory=True)
         usr_eval_host(self.ctx, n, xyzq.data_ptr(), out.data_ptr(), energy.data_ptr(), stream)
         return out, energy
+
+    def virial(self):
+        """3 x 3 float64 CUDA tensor: the virial of the last evaluation (virial=1 contexts)."""
+        import torch
+        W = torch.empty(9, dtype=torch.float64, device="cuda")
+        usr_virial(self.ctx, W.data_ptr())
+        return W.view(3, 3)
 
     def debug_cells(self, xyzq):
         import torch
