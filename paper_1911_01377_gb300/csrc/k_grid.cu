@@ -32,7 +32,7 @@ namespace usr {
 
 namespace {
 
-constexpr int kThreads = 512;          // 16 warps: one CTA per block of cells keeps the halo small, so each CTA carries many warps
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;         // atoms whose weights are staged at once (spread)
 constexpr int kGChunk = 128;        // atoms staged at once (gather)
@@ -120,7 +120,7 @@ __device__ __forceinline__ int block_atom(int j, const int* rs, const int* pre)
 /* ------------------------------------------------------------------ spread */
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 1) k_spread(const float4* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start, GridArgs g,
                                                         float* __restrict__ tilebuf, double* __restrict__ partial,
                                                         unsigned int* __restrict__ counter,
@@ -389,7 +389,7 @@ void launch_virial_finalize(const double* near_w, int nwarps, const double* dots
 /* ------------------------------------------------------------------ gather */
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 1) k_gather(const float4* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start,
                                                         const int* __restrict__ perm,
                                                         const float4* __restrict__ near_out,
