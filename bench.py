@@ -14,7 +14,7 @@ run at r_c = 8 and 13 A, and two plain FP32 forms are timed beside it: FP32
 CUDA-core convolutions with the same spreading, and the tight FP32 form
 (12-point stencil, sigma_s = h) used for the 1e-5 parity tests.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--serve-systems M] [--scale]
 
 N > 1 (under torch.distributed.run): every rank evaluates its own replica of
 the workload (independent systems, no collective), value sums all ranks over
@@ -161,13 +161,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream):
+def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWEEP):
     """Device-time `steps` sweeps of one form; returns (total ms, per-stage ms sums, contexts, outs, ens)."""
     name, conv, P, ratio = form
     ctxs = [usr.USeries(w.box, w.grid, r_c, "C1_B2", max_atoms=w.n, conv=conv, spread_points=P,
-                        spread_sigma_over_h=ratio) for r_c in SWEEP]
-    outs = [torch.empty((w.n, 4), dtype=torch.float32, device=x.device) for _ in SWEEP]
-    ens = [torch.empty(4, dtype=torch.float64, device=x.device) for _ in SWEEP]
+                        spread_sigma_over_h=ratio) for r_c in cutoffs]
+    outs = [torch.empty((w.n, 4), dtype=torch.float32, device=x.device) for _ in cutoffs]
+    ens = [torch.empty(4, dtype=torch.float64, device=x.device) for _ in cutoffs]
 
     def step():
         for c, o, e in zip(ctxs, outs, ens):
@@ -182,7 +182,7 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream):
         if st != 0:
             raise usr.UsrError(st, f"device status after warm-up ({name})")
         usr.usr_set_profiling(c.ctx, True)
-    stage = [[0.0] * usr.USR_NSTAGES for _ in SWEEP]
+    stage = [[0.0] * usr.USR_NSTAGES for _ in cutoffs]
     total = 0.0
     for k in range(steps):
         flush.fill_(float(k % 7))
@@ -199,6 +199,27 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream):
     for c in ctxs:
         usr.usr_set_profiling(c.ctx, False)
     return total, stage, ctxs, outs, ens
+
+
+SCALE_FORMS = (CHOSEN, ("tf32x3_gse8", 1, 8, 0.83), COMPARATORS[0], COMPARATORS[1])
+
+
+def run_scale(usr, torch, steps, warmup, flush, stream):
+    """Precision forms at scale: 354,933 waters (1,064,799 charges), L = 220 A, r_c = 10 A,
+    176^3 grid; one evaluation per step per form, inputs resident, L2 flushed between steps.
+    The errors of these forms against the FP64 oracle are checked by the scale parity tests."""
+    from paper_1911_01377_gb300 import workloads as W
+    w = W.get("water_1m")
+    x = torch.from_numpy(w.xyzq).to(flush.device)
+    forms = {}
+    for form in SCALE_FORMS:
+        tms, stage, cc, _, _ = _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=(10.0,))
+        forms[form[0]] = {"value": w.n * steps / (tms / 1e3), "unit": UNIT, "ms_per_eval": tms / steps,
+                          "stage_ms": {k: v / steps for k, v in zip(usr.STAGES, stage[0])}}
+        for c in cc:
+            c.close()
+    return {"workload": f"water_1m: {w.n} charges (354933 3-site waters), cubic L=220 A, 176^3 grid, "
+                        f"C1 b=2, r_c=10 A", "forms": forms}
 
 
 def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_frac=0.7):
@@ -361,6 +382,7 @@ def run_gpu(args):
             c.close()
 
     serving = run_serving(usr, torch, args.serve_systems) if args.serve_systems > 0 else None
+    scale = run_scale(usr, torch, args.steps, args.warmup, flush, stream) if args.scale else None
 
     if rank != 0:
         if ws > 1:
@@ -410,6 +432,7 @@ def run_gpu(args):
         "accuracy": acc,
         "comparators": comparators,
         "serving": serving,
+        "scale_1m": scale,
         "roofline": roof,
         "stage_ms_mean": dict(zip(usr.STAGES, per_stage)),
         "cpu_baseline": {"value": n / t_cpu, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
@@ -433,6 +456,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--serve-systems", type=int, default=512,
                     help="systems in the serving stream (0 skips the serving measurement)")
+    ap.add_argument("--scale", action="store_true",
+                    help="also time the 1,064,799-charge water box (r_c = 10 A, 176^3 grid) in every form")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

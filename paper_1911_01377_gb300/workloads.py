@@ -14,6 +14,7 @@ waters, Sec. IV): a 40 A slab of chain-like beads between two water layers.
 """
 from __future__ import annotations
 
+import hashlib
 import math
 import os
 from dataclasses import dataclass, field
@@ -98,7 +99,8 @@ class _Hash:
             return np.full(p.shape[0], np.inf)
         c3 = self._cell3(p)
         nb = self._lin(np.mod(c3[:, None, :] + self._OFFS[None, :, :], self.nc))   # (m, 27)
-        ids = self.idx[nb].reshape(p.shape[0], -1)                                  # (m, 27 cap)
+        mf = max(1, int(self.fill.max()))                   # slots in use in the fullest cell
+        ids = self.idx[nb, :mf].reshape(p.shape[0], -1)                             # (m, 27 mf)
         valid = ids >= 0
         q = self._buf[np.where(valid, ids, 0)]                                      # (m, 27 cap, 3)
         d = q - p[:, None, :]
@@ -206,8 +208,28 @@ def _finish(name, box, grid, r_c, rows, description, **meta) -> Workload:
                     tuple(float(v) for v in r_c), xyzq, description, meta)
 
 
+def _disk_cached(name: str, make) -> np.ndarray:
+    """Rows of a large generated workload, kept in _cache/ next to this file under a
+    key that changes with this file's source (a generator change regenerates)."""
+    with open(__file__, "rb") as f:
+        key = hashlib.sha1(f.read()).hexdigest()[:16]
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_cache")
+    path = os.path.join(d, f"{name}-{key}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    rows = make()
+    os.makedirs(d, exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        np.save(f, rows)
+    os.replace(tmp, path)
+    return rows
+
+
 def water_workload(index: int, name: str, n_waters: int, L: float, r_c, grid) -> Workload:
-    rows = water_box(SEED_BASE + index, (L, L, L), n_waters)
+    def make():
+        return water_box(SEED_BASE + index, (L, L, L), n_waters)
+    rows = _disk_cached(name, make) if n_waters > 100000 else make()
     return _finish(name, (L, L, L), grid, r_c, rows,
                    f"{n_waters} rigid 3-site waters ({3 * n_waters} charges), cubic box L={L} A")
 

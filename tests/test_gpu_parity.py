@@ -254,10 +254,9 @@ def test_tensor_core_ragged_lines(torch_cuda, conv):
     xyzq = W.random_neutral(77, 2400, box, min_dist=1.3)
     w = W.Workload("tc_ragged", box, (24, 32, 264), (7.0,), xyzq, "tensor-core ragged shapes")
     ref = O.evaluate(O.Series(*usr_series_tuple("C1_B2")), 7.0, w.box, w.xyzq[:, :3], w.xyzq[:, 3])
-    _, g32 = gpu_eval(torch, w, 7.0)
     _, gtc = gpu_eval(torch, w, 7.0, conv=conv)
     tol = TC_TOL[conv]
-    assert O.rms_rel(gtc["far"][:, 3], g32["far"][:, 3]) < tol["F"]
+    assert O.rms_rel(gtc["far"][:, 3], ref.phi_far) < 2 * tol["F"]
     assert O.rms_rel(gtc["out"][:, :3], ref.F) < tol["F"]
     # the z pass here contracts K = 7 terms x 264 points = 1848 per output on the
     # tensor cores, whose FP32 accumulation rounds differently from the FP32

@@ -1,0 +1,108 @@
+"""Precision forms at scale: 354,933 rigid waters (1,064,799 charges) in a
+cubic box L = 220 A at 0.1 charges/A^3, r_c = 10 A, 176^3 grid, evaluated by
+the FP32 path and by the two tensor-core convolution forms (TF32x3, BF16x3;
+FP32 accumulation, hi/lo split operands, energies reduced in FP64).
+
+The FP64 oracle cannot give every atom's near sum at this size in test time,
+so the checks are on outputs it can compute one by one and on identities that
+hold at any size:
+
+  * 384 seeded random targets: near and far potentials and forces, and the
+    totals, against the oracle (direct near sum at the target; exact k-space
+    far part from the structure factor of all 1,064,799 charges);
+  * E_far against the oracle's k-space energy, E_self against -1/2 F(0) sum q^2
+    (Eq. 10's self term);
+  * E_near against 1/2 sum_i q_i phi_near,i of the same run (the energy and the
+    per-atom potentials are reduced separately on the device);
+  * the near part is bit-identical in all three forms (it does not depend on
+    the convolution form).
+
+The oracle's k-space sum stops at |k| s_min = 6.5, where the narrowest
+Gaussian's transform exp(-k^2 s^2 / 2) is below 7e-10 of its peak: a
+truncation far below every tolerance here.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_01377_gb300 import build as B
+from paper_1911_01377_gb300 import usr
+from paper_1911_01377_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+R_C = 10.0
+N_TARGETS = 384
+# rms relative tolerances per form: (near, far potential, far force, total potential, total force, E_far)
+TOL = {0: dict(far_phi=2e-5, far_F=1e-4, phi=1e-5, F=1e-5, E_far=2e-5),
+       1: dict(far_phi=2e-5, far_F=1e-4, phi=1e-5, F=1e-5, E_far=2e-5),
+       2: dict(far_phi=1e-4, far_F=1e-3, phi=1e-4, F=1e-4, E_far=1e-4)}
+TOL_NEAR = 2e-6
+
+
+@pytest.fixture(scope="module")
+def scale():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    B.build()
+    w = W.get("water_1m")
+    rng = np.random.default_rng(1064799)
+    targets = np.sort(rng.choice(w.n, N_TARGETS, replace=False)).astype(np.int32)
+    from tests.golden import paper_tables
+    ser = O.Series(*paper_tables()["table2_C1"])
+    _, s = O.terms(ser, R_C)
+    pos = w.xyzq[:, :3].astype(np.float64)
+    q = w.xyzq[:, 3].astype(np.float64)
+    ref = O.evaluate(ser, R_C, w.box, pos, q, targets=targets, kmax=6.5 / float(np.min(s)))
+    gpu = {}
+    x = torch.from_numpy(w.xyzq).cuda()
+    for conv in (0, 1, 2):
+        ctx = usr.USeries(w.box, w.grid, R_C, "C1_B2", max_atoms=w.n, conv=conv)
+        usr.usr_set_keep_parts(ctx.ctx, True)
+        out, en = ctx.eval(x)
+        near, far = ctx.parts(w.n)
+        torch.cuda.synchronize()
+        assert usr.usr_last_device_status(ctx.ctx) == 0
+        gpu[conv] = dict(out=out.cpu().numpy().astype(np.float64), E=en.cpu().numpy(),
+                         near=near.cpu().numpy().astype(np.float64), far=far.cpu().numpy().astype(np.float64))
+        ctx.close()
+    return w, targets, q, ref, gpu
+
+
+def test_near_at_targets(scale):
+    w, t, q, ref, gpu = scale
+    g = gpu[0]
+    assert O.rms_rel(g["near"][t, 3], ref.phi_near) < TOL_NEAR
+    assert O.rms_rel(g["near"][t, :3], ref.F_near) < TOL_NEAR
+    for conv in (1, 2):                                  # the near part does not depend on the form
+        assert np.array_equal(gpu[conv]["near"], g["near"])
+
+
+@pytest.mark.parametrize("conv", [0, 1, 2])
+def test_far_and_total_at_targets(scale, conv):
+    w, t, q, ref, gpu = scale
+    g, tol = gpu[conv], TOL[conv]
+    e = dict(far_phi=O.rms_rel(g["far"][t, 3], ref.phi_far), far_F=O.rms_rel(g["far"][t, :3], ref.F_far),
+             phi=O.rms_rel(g["out"][t, 3], ref.phi), F=O.rms_rel(g["out"][t, :3], ref.F))
+    print(f"\nwater_1m conv={conv}: " + " ".join(f"{k}={v:.3e}" for k, v in e.items()))
+    for k, v in e.items():
+        assert v < tol[k], k
+
+
+@pytest.mark.parametrize("conv", [0, 1, 2])
+def test_energies(scale, conv):
+    w, t, q, ref, gpu = scale
+    g = gpu[conv]["E"]
+    # magnitude of the far part's terms, 1/2 sum |q_i phi_far,i|, estimated from the targets
+    scale_far = 0.5 * w.n * np.mean(np.abs(q[t] * ref.phi_far))
+    print(f"\nwater_1m conv={conv}: E_far={g[2]:.9f} oracle={ref.E_far:.9f} "
+          f"rel_to_terms={abs(g[2] - ref.E_far) / scale_far:.3e}")
+    assert abs(g[2] - ref.E_far) < TOL[conv]["E_far"] * scale_far
+    assert abs(g[3] / ref.E_self - 1.0) < 1e-9
+    near = gpu[conv]["near"]
+    half_q_phi = 0.5 * float(np.dot(q, near[:, 3]))
+    scale_near = 0.5 * float(np.sum(np.abs(q * near[:, 3])))
+    assert abs(g[1] - half_q_phi) < 1e-6 * scale_near
+    assert abs(g[0] - (g[1] + g[2] + g[3])) < 1e-12 * abs(g[0])
+
