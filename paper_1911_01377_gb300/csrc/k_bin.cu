@@ -153,10 +153,31 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(const int* __restric
  * written to the padded layout at pstart[c] with dummy rows (q = 0, far
  * away and far apart, index -1) after the last atom; then each cluster's
  * bounding box.
+ *
+ * Cluster positions are stored paired for the pair kernel's two-wide FP32
+ * arithmetic: atom t of a cluster (t = 4 h + g, h = 0, 1) goes to the 32-byte
+ * group g as x at float 8 g + h, y at 8 g + 2 + h, z at 8 g + 4 + h and q at
+ * 8 g + 6 + h, so one lane's two 16-byte loads give (x_g, x_g+4), (y_g, y_g+4),
+ * (z_g, z_g+4), (q_g, q_g+4).
  */
 __device__ __forceinline__ int spread3(int v)
 {
     return (v & 1) | ((v & 2) << 2) | ((v & 4) << 4);
+}
+
+__device__ __forceinline__ int pk_off(int slot)
+{
+    const int t = slot & 7;
+    return (slot >> 3) * 32 + 8 * (t & 3) + (t >> 2);
+}
+
+__device__ __forceinline__ void pk_store(float* cp, int slot, float4 p)
+{
+    const int o = pk_off(slot);
+    cp[o] = p.x;
+    cp[o + 2] = p.y;
+    cp[o + 4] = p.z;
+    cp[o + 6] = p.w;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __restrict__ start,
@@ -174,6 +195,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
     const float ox = (float)cx / b.cs[0], oy = (float)cy / b.cs[1], oz = (float)cz / b.cs[2];
     const float kx = 8.0f * b.cs[0], ky = 8.0f * b.cs[1], kz = 8.0f * b.cs[2];
     const bool in_smem = m <= kSortMax;
+    float* cp = reinterpret_cast<float*>(cpos);
     int* kk = in_smem ? ks : key + s0;
     for (int e = threadIdx.x; e < m; e += kSortThreads) {
         const float4 p = spos[s0 + e];
@@ -190,13 +212,14 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
             const int kf = kk[f];
             r += (kf < ke) || (kf == ke && f < e);
         }
-        cpos[p0 + r] = spos[s0 + e];
+        pk_store(cp, p0 + r, spos[s0 + e]);
         cidx[p0 + r] = s0 + e;
     }
     for (int e = m + threadIdx.x; e < pm; e += kSortThreads) {
-        // padding rows: far from the box and 4e4 A apart, so no pair involving one is ever within r_c
+        // padding rows: far from the box, so never within r_c of an atom, and 4e4 A apart within
+        // a cluster (rows of different cells may coincide; the pair kernel never uses their sums)
         const float far = -1.0e6f - 4.0e4f * (float)(e & 7);
-        cpos[p0 + e] = make_float4(far, far, far, 0.0f);
+        pk_store(cp, p0 + e, make_float4(far, far, far, 0.0f));
         cidx[p0 + e] = -1;
     }
     __syncthreads();
@@ -205,7 +228,8 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
         for (int t = 0; t < 8; ++t) {
             const int sl = p0 + 8 * k + t;
             if (cidx[sl] < 0) continue;
-            const float4 p = cpos[sl];
+            const int o = pk_off(sl);
+            const float4 p = make_float4(cp[o], cp[o + 2], cp[o + 4], 0.f);
             lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
             hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
         }

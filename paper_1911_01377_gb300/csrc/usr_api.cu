@@ -517,6 +517,8 @@ void fill_args(usr_ctx* c)
     for (int e = 0; e < P.n_explicit; ++e) {
         a.ea[e] = (float)P.ea[e];
         a.einv[e] = (float)P.einv[e];
+        a.el2[e] = (float)(-P.einv[e] * 1.4426950408889634);    // log2(e)
+        a.ne2[e] = (float)(-2.0 * P.einv[e]);
     }
     for (int d = 0; d <= usr::kMaxPolyDeg; ++d) a.poly[d] = (float)P.poly[d];
     usr::GridArgs& g = c->grid;

@@ -104,6 +104,8 @@ struct NearArgs {
     int n_explicit;
     float ea[kMaxExplicit];
     float einv[kMaxExplicit];
+    float el2[kMaxExplicit];   // -einv log2(e): exp(-u einv) = 2^(u el2)
+    float ne2[kMaxExplicit];   // -2 einv: factor of 2 dF/du
     float poly[kMaxPolyDeg + 1];
 };
 
