@@ -44,9 +44,46 @@ SWEEP = (8.0, 9.0, 10.0, 11.0, 12.0, 13.0)
 # conv x, conv y, conv z, grid_mean, gather
 KERNELS_PER_EVAL = 13
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock
+# DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over the evaluation
+# launches of one ncu capture of `bench.py --steps 2 --warmup 3 --serve-systems 0`; None whenever the
+# pair kernel has changed since that capture
+NEAR_TRAFFIC_BYTES = 1.647e6
 # forms: (name, conv, spread_points, spread_sigma_over_h)
 CHOSEN = ("bf16x3_gse8", 2, 8, 0.83)
 COMPARATORS = (("fp32_gse8", 0, 8, 0.83), ("fp32_tight12", 0, 12, 1.0))
+
+
+def measured_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s measured on this machine's GPUs (MEASURED_PEAKS.json), else the
+    fallback figures of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def stage_floors(n, pairs, info, grid, spread_points, hilo_products, peaks):
+    """Lower bounds (ms) of one evaluation's stages from their algorithmic work and the peaks:
+    bin 60 B/atom of HBM (positions in, cell ids, permutation, sorted and paired copies);
+    near pairs x flops/pair at the FP32 peak; spread 2 P^3 and gather 8 P^3 flops per atom at the
+    FP32 peak (one FMA per stencil point; value and three gradient components); conv the larger of
+    its tensor flops (hilo_products x 2 N G n_axis per pass) at the BF16 peak and its grid bytes at the
+    HBM peak (4 G in and 4 N G out on x, 4 N G both ways on y, 4 N G in and 4 G out on z)."""
+    G = grid[0] * grid[1] * grid[2]
+    N = info.n_terms
+    fp32 = FP32_PEAK_TFLOPS * 1e12
+    hbm = peaks["hbm_gbs"] * 1e9
+    tc = peaks["bf16_tflops"] * 1e12
+    f = {"bin": 60.0 * n / hbm,
+         "near": pairs * near_flops_per_pair(info.poly_degree, info.n_explicit) / fp32,
+         "spread": 2.0 * spread_points ** 3 * n / fp32,
+         "gather": 8.0 * spread_points ** 3 * n / fp32}
+    byts = {"conv_x": 4.0 * G + 4.0 * N * G, "conv_y": 8.0 * N * G, "conv_z": 4.0 * N * G + 4.0 * G}
+    for ax, nx in zip(("conv_x", "conv_y", "conv_z"), grid):
+        f[ax] = max(hilo_products * 2.0 * N * G * nx / tc, byts[ax] / hbm)
+    return {k: 1e3 * v for k, v in f.items()}
 
 
 def near_flops_per_pair(poly_degree: int, n_explicit: int) -> int:
@@ -62,6 +99,23 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over all ranks (the slowest rank's time); x itself at world size 1.
+    Works with any initialised torch.distributed backend (NCCL on GPUs, gloo on CPUs)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; the job takes as long as its slowest rank."""
+    return units_per_rank * world_size / seconds_max
 
 
 class ClockSampler:
@@ -340,12 +394,9 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     evals = n * len(SWEEP) * args.steps * ws
-    value = evals / (total_ms / 1e3)
+    value = whole_job_rate(n * len(SWEEP) * args.steps, ws, total_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned memory, copies inside the timed region)
     xh = torch.from_numpy(w.xyzq).pin_memory()
@@ -361,11 +412,8 @@ def run_gpu(args):
             usr.usr_eval_host(c.ctx, n, xh.data_ptr(), o.data_ptr(), e.data_ptr(), stream)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = evals / t_e2e
+    t_e2e = max_over_ranks(t_e2e, dev)
+    e2e_value = whole_job_rate(n * len(SWEEP) * args.steps, ws, t_e2e)
     chosen_outs = [o.double().cpu().numpy() for o in outs]
     chosen_E = [float(e[0].item()) for e in ens]
     infos = [c.info for c in ctxs]
@@ -398,10 +446,21 @@ def run_gpu(args):
         t_dom = sum(stage_ms[k][dom] for k in range(len(SWEEP))) / args.steps / 1e3
         achieved = flops / t_dom / 1e12
         roof = {"kernel": "near (k_near_cl)", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NEAR_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz maximum SM clock",
                 "flops_per_pair": [near_flops_per_pair(i.poly_degree, i.n_explicit) for i in infos],
                 "pairs_per_eval": pairs}
+
+    # stage-wise floors of the chosen form, summed over the sweep, against the measured stage times
+    peaks = measured_peaks()
+    floors = [stage_floors(n, p, i, w.grid, CHOSEN[2], 3, peaks) for p, i in zip(pairs, infos)]
+    floor_ms = {st: sum(fl[st] for fl in floors) / len(SWEEP) for st in usr.STAGES}
+    stage_roof = {"floor_ms_mean": floor_ms, "measured_ms_mean": dict(zip(usr.STAGES, per_stage)),
+                  "frac_of_stage_sum": sum(floor_ms.values()) / sum(per_stage),
+                  "peaks": {"fp32_tflops": FP32_PEAK_TFLOPS, "hbm_gbs": peaks["hbm_gbs"],
+                            "bf16_tflops": peaks["bf16_tflops"],
+                            "source": f"FP32 derived; HBM and BF16 {peaks['source']} (MEASURED_PEAKS.json)"}}
 
     # accuracy of every form against the FP64 oracle at r_c = 8 (full) and the chosen form at 13
     t0 = time.perf_counter()
@@ -435,6 +494,7 @@ def run_gpu(args):
         "scale_1m": scale,
         "roofline": roof,
         "stage_ms_mean": dict(zip(usr.STAGES, per_stage)),
+        "stage_roofline": stage_roof,
         "cpu_baseline": {"value": n / t_cpu, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"one full FP64 oracle evaluation (E, all forces and potentials) of the "
                                    f"{n}-charge slab at r_c = 8 A, {t_cpu:.1f} s"},
