@@ -2,8 +2,8 @@
 
     python -m paper_1911_01377_gb300 --workload membrane_slab --rc 10 --evals 3
 
-Prints the energy breakdown and the per-stage times (CUDA events) of the last
-evaluation.  Useful for profiling a single evaluation under a tool such as ncu.
+Prints the energy breakdown and the per-stage times (CUDA events), averaged over
+the evaluations after the first.  Useful for profiling a single evaluation under a tool such as ncu.
 """
 from __future__ import annotations
 
@@ -38,8 +38,11 @@ def main(argv=None):
     x = torch.from_numpy(w.xyzq).cuda()
     out = torch.empty((w.n, 4), dtype=torch.float32, device="cuda")
     en = torch.empty(4, dtype=torch.float64, device="cuda")
-    for _ in range(args.evals):
+    acc = [0.0] * usr.USR_NSTAGES
+    for k in range(args.evals):
         ctx.eval(x, out, en)
+        if k > 0 or args.evals == 1:               # the first of several evaluations is a warm-up
+            acc = [a + v for a, v in zip(acc, usr.usr_stage_times(ctx.ctx))]
     torch.cuda.synchronize()
     st = usr.usr_last_device_status(ctx.ctx)
     if st != 0:
@@ -50,8 +53,8 @@ def main(argv=None):
     print(f"E={e[0]:.10f} E_near={e[1]:.10f} E_far={e[2]:.10f} E_self={e[3]:.10f}")
     if args.virial:
         print("virial:", ctx.virial().cpu().numpy().round(6).tolist())
-    ms = usr.usr_stage_times(ctx.ctx)
-    print("stage ms: " + " ".join(f"{k}={v:.4f}" for k, v in zip(usr.STAGES, ms)) + f" total={sum(ms):.4f}")
+    ms = [a / max(1, args.evals - 1) if args.evals > 1 else a for a in acc]
+    print("stage ms (mean): " + " ".join(f"{k}={v:.4f}" for k, v in zip(usr.STAGES, ms)) + f" total={sum(ms):.4f}")
     ctx.close()
 
 

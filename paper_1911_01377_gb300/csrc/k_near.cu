@@ -104,7 +104,7 @@ __device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
  * Lane (il = lane / 4, g = lane % 4) holds i atom il and, for every cluster pair, the two
  * j atoms g and g + 4 of the j cluster (the paired layout of k_cluster_build).
  */
-template <int DEG, bool COUNT, bool VIR>
+template <int DEG, int NEXP, bool COUNT, bool VIR>
 __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos, const int* __restrict__ cidx,
                                                  const int* __restrict__ ccell, const float4* __restrict__ bblo,
                                                  const float4* __restrict__ bbhi, const int* __restrict__ pstart,
@@ -200,7 +200,10 @@ __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos
                         p = fma2(p, s, dup(a.poly[d]));
                     }
                     f2 d2 = mul2(dp, c_d2);                                 // 2 dF/du
-                    for (int e = 0; e < a.n_explicit; ++e) {
+                    // NEXP >= 0: that many explicit Gaussians, unrolled; -1: a.n_explicit of them
+                    const int nexp = NEXP >= 0 ? NEXP : a.n_explicit;
+                    #pragma unroll
+                    for (int e = 0; e < nexp; ++e) {
                         float ea_, eb_;
                         upk(mul2(u, dup(a.el2[e])), ea_, eb_);
                         const f2 gg = mul2(pk(exp2_ftz(ea_), exp2_ftz(eb_)), dup(a.ea[e]));
@@ -273,18 +276,32 @@ __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos
     }
 }
 
-template <int DEG, bool COUNT>
+template <int DEG, int NEXP, bool COUNT>
 static void launch_cl(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
                       const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, float4* out,
                       int* count, unsigned long long* hash, cudaStream_t st, double* vir = nullptr)
 {
     const int blocks = (max_clusters + 3) / 4;
     if (vir)
-        k_near_cl<DEG, COUNT, true><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out, count,
-                                                             hash, vir);
+        k_near_cl<DEG, NEXP, COUNT, true><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out,
+                                                                   count, hash, vir);
     else
-        k_near_cl<DEG, COUNT, false><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, out,
-                                                              count, hash, nullptr);
+        k_near_cl<DEG, NEXP, COUNT, false><<<blocks, 128, 0, st>>>(cpos, cidx, ccell, bblo, bbhi, pstart, perm, a,
+                                                                    out, count, hash, nullptr);
+}
+
+/* One explicit Gaussian (the common case: the narrow j = 0 term) unrolled, any other count in a loop. */
+template <int DEG>
+static void launch_deg(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
+                       const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st,
+                       double* vir)
+{
+    if (a.n_explicit == 1)
+        launch_cl<DEG, 1, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr,
+                                 nullptr, st, vir);
+    else
+        launch_cl<DEG, -1, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr,
+                                  nullptr, st, vir);
 }
 
 int near_warps(int max_clusters) { return 4 * ((max_clusters + 3) / 4); }
@@ -293,14 +310,14 @@ void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx,
                  const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st, double* vir)
 {
     switch (deg) {
-        case 6: launch_cl<6, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 7: launch_cl<7, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 8: launch_cl<8, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 10: launch_cl<10, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 12: launch_cl<12, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 16: launch_cl<16, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        case 20: launch_cl<20, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
-        default: launch_cl<24, false>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, nullptr, a, out, nullptr, nullptr, st, vir); break;
+        case 6: launch_deg<6>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 7: launch_deg<7>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 8: launch_deg<8>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 10: launch_deg<10>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 12: launch_deg<12>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 16: launch_deg<16>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        case 20: launch_deg<20>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
+        default: launch_deg<24>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, a, out, st, vir); break;
     }
 }
 
@@ -308,7 +325,7 @@ void launch_pairs(int max_clusters, const float4* cpos, const int* cidx, const i
                   const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, int* count,
                   unsigned long long* hash, cudaStream_t st)
 {
-    launch_cl<8, true>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, nullptr, count, hash, st);
+    launch_cl<8, 0, true>(max_clusters, cpos, cidx, ccell, bblo, bbhi, pstart, perm, a, nullptr, count, hash, st);
 }
 
 }  // namespace usr

@@ -344,7 +344,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     }
     // cell blocks of the spreading / interpolation kernels: cores of about 16
     // grid points (the tiles' halo of P + 3 points makes small cores costly),
-    // tiles within kTileMaxSmem, at least 128 blocks when the cell list allows,
+    // tiles within kTileMaxSmem, at least 304 blocks (two per SM) when the cell list allows,
     // at most 64 (z, y) cell rows per block
     {
         TileGeom& tg = P.tile;
@@ -371,7 +371,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             return true;
         };
         while ((bytes() > kTileMaxSmem || tg.kb[1] * tg.kb[2] > 64) && shrink()) {}
-        while (nblocks() < 128 && shrink()) {}
+        while (nblocks() < 304 && shrink()) {}
         if (bytes() > kTileMaxSmem) return USR_ERR_BOX;
         for (int a = 0; a < 3; ++a) {
             tg.nbk[a] = (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
