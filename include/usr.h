@@ -173,6 +173,9 @@ usr_status usr_info(const usr_ctx* ctx, usr_plan_info* out);
  *          phi_i = dE/dq_i (the potential at i with i's self term included)
  *   energy device, 4 doubles: E, E_near, E_far, E_self (may be NULL)
  * n = 0 writes zero energies.  USR_ERR_CAPACITY if n > max_atoms.
+ * Internally the far part runs on a second stream of the context, forked from
+ * `stream` after the cell list and joined back before the interpolation, so
+ * the call stays ordered on `stream` (and capturable) as one unit.
  */
 usr_status usr_eval(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
 
@@ -333,12 +336,15 @@ usr_status usr_debug_parts(usr_ctx* ctx, float* near_out, float* far_out, void* 
 
 enum { USR_NSTAGES = 7 };  /* bin, near, spread, conv_x, conv_y, conv_z, gather */
 
-/* Record CUDA events between the stages of every usr_eval (on its stream). */
+/* Record CUDA events between the stages of every usr_eval. */
 usr_status usr_set_profiling(usr_ctx* ctx, int on);
 
 /*
  * Milliseconds of each stage of the last profiled usr_eval (synchronises).
- * ms must hold USR_NSTAGES floats.
+ * ms must hold USR_NSTAGES floats.  The far chain (spread, conv_x/y/z, and the
+ * psi mean, counted in gather) runs on the context's own high-priority stream,
+ * concurrently with the near stage on the caller's stream, so the stages can
+ * add up to more than the evaluation's duration.
  */
 usr_status usr_stage_times(usr_ctx* ctx, float* ms);
 

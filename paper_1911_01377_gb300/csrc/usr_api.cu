@@ -20,6 +20,9 @@
 
 using usr::Plan;
 
+// profiling events of one evaluation (stage boundaries on the two streams)
+constexpr int kProfEvents = 11;
+
 struct usr_ctx {
     Plan plan;
     int device = 0;
@@ -74,10 +77,14 @@ struct usr_ctx {
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
     bool keep_parts = false;
     bool parts_valid = false;
-    // profiling
+    // the far chain (spread, convolutions, psi mean) runs on `side`, a high-priority stream forked from and
+    // joined back to the caller's stream, while the pair kernel runs on the caller's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // profiling: stage boundary events (see usr_stage_times)
     bool prof = false;
     bool prof_valid = false;
-    cudaEvent_t ev[USR_NSTAGES + 1];
+    cudaEvent_t ev[kProfEvents];
     bool ev_made = false;
     cudaStream_t last_stream = nullptr;
     int last_n = 0;
@@ -118,6 +125,9 @@ void free_all(usr_ctx* c)
             if (p) cudaFree(p);
     if (c->ev_made)
         for (auto& e : c->ev) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     if (c->h_stage) cudaFreeHost(c->h_stage);
 }
@@ -613,37 +623,51 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         c->vir_valid = c->vir;
         return USR_OK;
     }
-    auto mark = [&](int k) {
-        if (c->prof) cudaEventRecord(c->ev[k], st);
+    // stage boundaries: on the caller's stream 0 start, 1 cell list done, 2 pair kernel done, 9 gather
+    // may start (the far chain joined), 10 end; on the side stream 3 start, 4 spread done, 5-7 passes
+    // x, y, z done, 8 psi mean done
+    auto mark = [&](int k, cudaStream_t s) {
+        if (c->prof) cudaEventRecord(c->ev[k], s);
     };
-    mark(0);
+    mark(0, st);
     bin_and_cluster(c, n, xyzq, st);
-    mark(1);
-    usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
-                     c->d_pstart, c->near, c->d_near, st, c->vir ? c->d_vnear : nullptr);
-    mark(2);
+    mark(1, st);
+    // fork: the far chain on the side stream (first, so that its few large CTAs are placed before the
+    // pair kernel's many small ones fill the SMs), the pair kernel on the caller's stream
+    if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev_fork, 0) != cudaSuccess)
+        return USR_ERR_CUDA;
+    cudaStream_t sd = c->side;
+    mark(3, sd);
     if (c->tc)
         usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
-                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st,
+                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd,
                            c->vir ? c->d_rho32 : nullptr);
     else
         usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
-                           c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, st);
-    mark(3);
+                           c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd);
+    mark(4, sd);
     if (c->tc) {
         for (int p = 0; p < 3; ++p) {
-            usr::launch_conv_tc(c->tc_bf16, c->maps[p], c->targs[p], c->tbatches[p], st);
-            mark(4 + p);
+            usr::launch_conv_tc(c->tc_bf16, c->maps[p], c->targs[p], c->tbatches[p], sd);
+            mark(5 + p, sd);
         }
     } else {
         float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
-        fp32_conv(c, c->d_rho, t, c->d_psi, st, [&](int k) { mark(4 + k); });
+        fp32_conv(c, c->d_rho, t, c->d_psi, sd, [&](int k) { mark(5 + k, sd); });
     }
-    usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, st);
+    usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
+    mark(8, sd);
+    if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
+    usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
+                     c->d_pstart, c->near, c->d_near, st, c->vir ? c->d_vnear : nullptr);
+    mark(2, st);
+    // join
+    if (cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return USR_ERR_CUDA;
+    mark(9, st);
     usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, out,
                        c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
                        c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
-    mark(7);
+    mark(10, st);
     if (c->vir) {
         // far virial: 1/2 <rho, psi_ab> per strain component, then the finalisation with E_far
         const float* rho = c->tc ? c->d_rho32 : c->d_rho;
@@ -701,6 +725,14 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
         return fail(USR_ERR_CUDA);
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->ev_made = true;
+    {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(USR_ERR_CUDA);
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(USR_ERR_CUDA);
     *out = c;
     return USR_OK;
@@ -872,11 +904,17 @@ extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
 {
     if (!c || !ms) return USR_ERR_ARG;
     if (!c->prof_valid) return USR_ERR_ARG;
-    if (cudaEventSynchronize(c->ev[USR_NSTAGES]) != cudaSuccess) return USR_ERR_CUDA;
+    if (cudaEventSynchronize(c->ev[10]) != cudaSuccess) return USR_ERR_CUDA;
+    // (from, to) event pairs of the stages; the gather stage adds the psi mean (8 - 7) to the gather itself
+    // (10 - 9); the wait for the later of the two branches (between 2 or 8 and 9) is in no stage
+    static const int from[USR_NSTAGES] = {0, 1, 3, 4, 5, 6, 9}, to[USR_NSTAGES] = {1, 2, 4, 5, 6, 7, 10};
     for (int k = 0; k < USR_NSTAGES; ++k) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]) != cudaSuccess) return USR_ERR_CUDA;
+        if (cudaEventElapsedTime(&t, c->ev[from[k]], c->ev[to[k]]) != cudaSuccess) return USR_ERR_CUDA;
         ms[k] = t;
     }
+    float gm = 0.f;
+    if (cudaEventElapsedTime(&gm, c->ev[7], c->ev[8]) != cudaSuccess) return USR_ERR_CUDA;
+    ms[USR_NSTAGES - 1] += gm;
     return USR_OK;
 }
