@@ -47,7 +47,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA)
 # DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over the evaluation
 # launches of one ncu capture of `bench.py --steps 2 --warmup 3 --serve-systems 0`; None whenever the
 # pair kernel has changed since that capture
-NEAR_TRAFFIC_BYTES = None
+NEAR_TRAFFIC_BYTES = 1.643e6
 # forms: (name, conv, spread_points, spread_sigma_over_h)
 CHOSEN = ("bf16x3_gse8", 2, 8, 0.83)
 COMPARATORS = (("fp32_gse8", 0, 8, 0.83), ("fp32_tight12", 0, 12, 1.0))
