@@ -40,9 +40,9 @@ METRIC = "u-series E+F atom-evals/s at rms rel force err ≤1e-4; serving p50/p9
 UNIT = "atom-evals/s"
 WORKLOAD = "membrane_slab"
 SWEEP = (8.0, 9.0, 10.0, 11.0, 12.0, 13.0)
-# kernels of one evaluation: bin_count, scan, place, cell_sort, cluster_build, near, spread, tile_reduce,
-# conv x, conv y, conv z, grid_mean, gather
-KERNELS_PER_EVAL = 13
+# kernels of one evaluation: bin_count, scan, place, cell_build, near, spread, tile_reduce, conv x, conv y,
+# conv z, grid_mean, gather
+KERNELS_PER_EVAL = 12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock
 # DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over the evaluation
 # launches of one ncu capture of `bench.py --steps 2 --warmup 3 --serve-systems 0`; None whenever the

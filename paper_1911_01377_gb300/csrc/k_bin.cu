@@ -8,6 +8,7 @@
  *   place       scatter caller indices into their cell's range
  *   cell_sort   order each cell's atoms by caller index (a stable, run-to-run
  *               deterministic order) and gather the sorted float4 rows
+ *   cell_build  the same sort fused with the pair kernel's 8-atom clusters
  *
  * Predicate (per axis, RN rounding, no contraction):
  *   k = floorf(x * invL); xw = fmaf(-k, L, x); if (xw < 0) xw += L;
@@ -180,29 +181,52 @@ __device__ __forceinline__ void pk_store(float* cp, int slot, float4 p)
     cp[o + 6] = p.w;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __restrict__ start,
-                                                                const int* __restrict__ pstart,
-                                                                const float4* __restrict__ spos, BoxF b,
-                                                                int* __restrict__ key, float4* __restrict__ cpos,
-                                                                int* __restrict__ cidx, int* __restrict__ ccell,
-                                                                float4* __restrict__ bblo, float4* __restrict__ bbhi)
+__device__ __forceinline__ int morton_key(float4 p, float ox, float oy, float oz, float kx, float ky, float kz)
 {
+    const int ix = min(7, max(0, (int)((p.x - ox) * kx)));
+    const int iy = min(7, max(0, (int)((p.y - oy) * ky)));
+    const int iz = min(7, max(0, (int)((p.z - oz) * kz)));
+    return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
+/*
+ * The cell sort and the clusters in one pass, one CTA per cell: first the
+ * cell's atoms in caller-index order (perm, sorted rows) with the Morton key
+ * of each sorted row, then the cluster order from the keys (as above).
+ */
+__global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restrict__ start,
+                                                             const int* __restrict__ pstart,
+                                                             const int* __restrict__ unsorted,
+                                                             const float4* __restrict__ wpos, BoxF b,
+                                                             int* __restrict__ perm, float4* __restrict__ spos,
+                                                             int* __restrict__ key, float4* __restrict__ cpos,
+                                                             int* __restrict__ cidx, int* __restrict__ ccell,
+                                                             float4* __restrict__ bblo, float4* __restrict__ bbhi)
+{
+    __shared__ int v[kSortMax];
     __shared__ int ks[kSortMax];
     const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
     const int p0 = pstart[c], pm = pstart[c + 1] - p0;
+    if (pm == 0) return;                                  // an empty cell has no clusters
     const int cx = c % b.nc[0], cy = (c / b.nc[0]) % b.nc[1], cz = c / (b.nc[0] * b.nc[1]);
     const float ox = (float)cx / b.cs[0], oy = (float)cy / b.cs[1], oz = (float)cz / b.cs[2];
     const float kx = 8.0f * b.cs[0], ky = 8.0f * b.cs[1], kz = 8.0f * b.cs[2];
     const bool in_smem = m <= kSortMax;
     float* cp = reinterpret_cast<float*>(cpos);
+    if (in_smem)
+        for (int e = threadIdx.x; e < m; e += kSortThreads) v[e] = unsorted[s0 + e];
+    __syncthreads();
+    const int* src = in_smem ? v : unsorted + s0;
     int* kk = in_smem ? ks : key + s0;
     for (int e = threadIdx.x; e < m; e += kSortThreads) {
-        const float4 p = spos[s0 + e];
-        int ix = min(7, max(0, (int)((p.x - ox) * kx)));
-        int iy = min(7, max(0, (int)((p.y - oy) * ky)));
-        int iz = min(7, max(0, (int)((p.z - oz) * kz)));
-        kk[e] = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+        const int x = src[e];
+        int r = 0;
+        for (int f = 0; f < m; ++f) r += src[f] < x;
+        const float4 p = wpos[x];
+        perm[s0 + r] = x;
+        spos[s0 + r] = p;
+        kk[r] = morton_key(p, ox, oy, oz, kx, ky, kz);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m; e += kSortThreads) {
@@ -240,12 +264,6 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
     }
 }
 
-void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
-                     int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st)
-{
-    k_cluster_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, spos, b, key, cpos, cidx, ccell, bblo, bbhi);
-}
-
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                 float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
                 cudaStream_t st)
@@ -256,6 +274,21 @@ void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count,
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
     k_cell_sort<<<ncell, kSortThreads, 0, st>>>(cell_start, unsorted, wpos, perm, spos);
+}
+
+/* The pair kernel's full cell list: counts, scan, placement, then the sort and the clusters fused per cell. */
+void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                      float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
+                      float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, int* status, cudaStream_t st)
+{
+    cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
+    int nb = (n + 255) / 256;
+    k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
+    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
+    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
+    // slot[] is free after placement: it holds the Morton keys of cells too large for shared memory
+    k_cell_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, unsorted, wpos, b, perm, spos, slot, cpos, cidx,
+                                                  ccell, bblo, bbhi);
 }
 
 }  // namespace usr

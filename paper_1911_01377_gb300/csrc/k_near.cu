@@ -5,7 +5,7 @@
  * over all j != i and periodic images.
  *
  * Cluster-pair scheme: each cell's atoms come in 8-atom spatial clusters
- * (k_cluster_build).  One warp owns one i-cluster; lanes are (i = lane / 4,
+ * (k_cell_build).  One warp owns one i-cluster; lanes are (i = lane / 4,
  * j = lane % 4), so a warp step evaluates an 8 x 4 block of pairs with every
  * lane on the same path.  The warp walks the j-clusters of the 27 neighbour
  * cells (edge >= r_c, >= 3 per axis, so every image appears once), tests 32
@@ -102,7 +102,7 @@ __device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
  * warp of the grid).
  *
  * Lane (il = lane / 4, g = lane % 4) holds i atom il and, for every cluster pair, the two
- * j atoms g and g + 4 of the j cluster (the paired layout of k_cluster_build).
+ * j atoms g and g + 4 of the j cluster (the paired layout of k_cell_build).
  */
 template <int DEG, int NEXP, bool COUNT, bool VIR>
 __global__ void __launch_bounds__(128) k_near_cl(const float4* __restrict__ cpos, const int* __restrict__ cidx,

@@ -554,10 +554,9 @@ usr_status check_device(const usr_ctx* c)
 /* Cell list (canonical sorted order) and the 8-atom clusters built from it. */
 void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
 {
-    usr::launch_bin(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos, c->d_cell_start,
-                    c->d_pstart, c->d_unsorted, c->d_perm, c->d_spos, c->d_status, st);
-    usr::launch_clusters(c->ncell, c->d_cell_start, c->d_pstart, c->d_spos, c->boxf, c->d_slot, c->d_cpos,
-                         c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, st);
+    usr::launch_bin_cells(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
+                          c->d_cell_start, c->d_pstart, c->d_unsorted, c->d_perm, c->d_spos, c->d_cpos, c->d_cidx,
+                          c->d_ccell, c->d_bblo, c->d_bbhi, c->d_status, st);
 }
 
 /* The evaluation sequence; xyzq/out are device pointers already checked. */

@@ -171,8 +171,9 @@ struct ConvTcMaps {
 void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                 float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
                 cudaStream_t st);
-void launch_clusters(int ncell, const int* cell_start, const int* pstart, const float4* spos, const BoxF& b,
-                     int* key, float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, cudaStream_t st);
+void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                      float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
+                      float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, int* status, cudaStream_t st);
 void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
                  const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st,
                  double* vir = nullptr);
