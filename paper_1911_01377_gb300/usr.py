@@ -19,6 +19,8 @@ _c_p = ctypes.c_void_p
 
 USR_OK = 0
 USR_NSTAGES = 7
+# usr_conv: convolution form of the far part
+USR_CONV_FP32, USR_CONV_TF32X3, USR_CONV_BF16X3 = 0, 1, 2
 STAGES = ("bin", "near", "spread", "conv_x", "conv_y", "conv_z", "gather")
 PRESETS = {"C0_B2": 0, "C1_B2": 1, "C2_B2": 2, "T1_A": 3, "T1_B": 4, "T1_C": 5}
 
