@@ -45,6 +45,29 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+/*
+ * Compensated FP32 accumulation (Neumaier): s + c carries the sum to about FP32 rounding of the total,
+ * independent of the number of terms.  FP64 is kept for the sums across threads: GB300's FP64 rate is
+ * about 1/64 of FP32, so per-element FP64 arithmetic in these kernels cost more than their FP32 work.
+ */
+struct CSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s));
+        s = t;
+    }
+    // a * b exactly, as the rounded product and its rounding error (fmaf gives the error exactly)
+    __device__ __forceinline__ void add_product(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        add(p);
+        add(fmaf(a, b, -p));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __device__ __forceinline__ float warp_sum_f(float v)
 {
     #pragma unroll
@@ -212,15 +235,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
     }
 
     // store the tile, sum it in a fixed order
-    double local = 0.0;
+    double local;
     {
         const float4* t4 = smem4;
         float4* out4 = reinterpret_cast<float4*>(tilebuf + (size_t)blockIdx.x * TT);
+        CSum cs;
         for (int t = threadIdx.x; t < (TT >> 2); t += kThreads) {
             const float4 v = t4[t];
             out4[t] = v;
-            local += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+            cs.add(v.x);
+            cs.add(v.y);
+            cs.add(v.z);
+            cs.add(v.w);
         }
+        local = cs.value();
     }
     local = warp_sum_d(local);
     if (lane == 0) red[warp] = local;
@@ -285,7 +313,7 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
             }
         }
     }
-    const float v = (float)((double)s - *mean);
+    const float v = s - (float)*mean;
     if (SPLIT != 0 && rho32) rho32[idx] = v;     // FP32 copy for the virial convolutions
     if (SPLIT == 0) {
         static_cast<float*>(rho)[idx] = v;
@@ -317,10 +345,13 @@ __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __r
     __shared__ double red[8];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double s = 0.0;
+    CSum cs;
     for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
-        s += w ? (double)psi[i] * (double)w[i] : (double)psi[i];
-    s = warp_sum_d(s);
+        if (w)
+            cs.add_product(psi[i], w[i]);
+        else
+            cs.add(psi[i]);
+    double s = warp_sum_d(cs.value());
     if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -433,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict
     // the stencil columns jx = u, u + 4, ... of every row, contracting z first
     constexpr int NC = (P + 3) / 4;
     const int quad = lane >> 2, u = lane & 3;
-    double e_tot = 0.0, e_near = 0.0, e_far = 0.0, e_self = 0.0;
+    CSum qn, qf, qq;                                       // sums of q phi_near, q phi_far, q^2
     const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
     for (int c0 = 0; c0 < natoms; c0 += kGChunk) {
         const int nch = min(kGChunk, natoms - c0);
@@ -530,17 +561,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict
                 out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
                 if (near_dbg) near_dbg[i] = nr;
                 if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
-                const double en = 0.5 * (double)qi * (double)nr.w;
-                const double ef = 0.5 * (double)qi * (double)aphi;
-                const double es = -0.5 * g.F0d * (double)qi * (double)qi;
-                e_near += en;
-                e_far += ef;
-                e_self += es;
-                e_tot += en + ef + es;
+                qn.add_product(qi, nr.w);
+                qf.add_product(qi, aphi);
+                qq.add_product(qi, qi);
             }
         }
     }
     // per-warp energy sums in a fixed order (lanes 0, 4, ..., 28 hold atoms)
+    double e_near = 0.5 * qn.value(), e_far = 0.5 * qf.value(), e_self = -0.5 * g.F0d * qq.value();
+    double e_tot = e_near + e_far + e_self;
     e_tot = warp_sum_d(e_tot);
     e_near = warp_sum_d(e_near);
     e_far = warp_sum_d(e_far);
