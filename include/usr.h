@@ -175,7 +175,9 @@ usr_status usr_info(const usr_ctx* ctx, usr_plan_info* out);
  * n = 0 writes zero energies.  USR_ERR_CAPACITY if n > max_atoms.
  * Internally the far part runs on a second stream of the context, forked from
  * `stream` after the cell list and joined back before the interpolation, so
- * the call stays ordered on `stream` (and capturable) as one unit.
+ * the call stays ordered on `stream` (and capturable) as one unit.  A context's
+ * buffers are reused by every call: calls on one context from different
+ * streams must be ordered by the caller (an event between them).
  */
 usr_status usr_eval(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
 
