@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
     constexpr int PA = (P + 3) & ~3;              // weight rows padded to 16 bytes
     __shared__ __align__(16) float W[kChunk][3][PA];
     __shared__ int B[kChunk][3];
+    __shared__ int2 R[kChunk];                    // (tile offset of the stencil corner or -1, its y)
     __shared__ float4 sp[kChunk];
     __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
     __shared__ double red[kWarps];
@@ -203,24 +204,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
             }
         }
         __syncthreads();
+        // phase 1b: one record per atom, the tile offset of its stencil corner (or -1) and its y
+        for (int a = threadIdx.x; a < nch; a += kThreads) {
+            const int bx = B[a][0], by = B[a][1], bz = B[a][2];
+            R[a] = make_int2(bx < 0 || by < 0 || bz < 0 ? -1 : (bz * Ty + by) * Tx + bx, by);
+        }
+        __syncthreads();
         // phase 2: warp w owns the tile rows ty = w (mod 8); for each atom it adds
         // the stencil columns of its one or two rows.  Lane = (column jx, group of
         // planes): P columns x G groups, each lane updating PG consecutive planes.
         {
             constexpr int G = 32 / P;                  // plane groups per row
             constexpr int PG = (P + G - 1) / G;        // planes per lane
+            static_assert((kWarps & (kWarps - 1)) == 0, "row ownership by a mask");
             const int jx = lane % P, grp = lane / P;
             const int k0 = grp * PG;
+            float* const tl = tile + k0 * TXY + jx;
             for (int a = 0; a < nch; ++a) {
-                const int bx = B[a][0], by = B[a][1], bz = B[a][2];
-                if (bx < 0 || by < 0 || bz < 0 || grp >= G) continue;
+                const int2 r = R[a];
+                if (r.x < 0 || grp >= G) continue;
                 float wz[PG];
                 #pragma unroll
                 for (int k = 0; k < PG; ++k) wz[k] = (k0 + k < P) ? W[a][2][k0 + k] : 0.f;
                 const float wxa = W[a][0][jx];
-                for (int jy = ((warp - by) % kWarps + kWarps) % kWarps; jy < P; jy += kWarps) {
+                for (int jy = (warp - r.y) & (kWarps - 1); jy < P; jy += kWarps) {
                     const float v = wxa * W[a][1][jy];
-                    float* col = tile + (((bz + k0) * Ty + by + jy) * Tx + bx + jx);
+                    float* col = tl + r.x + jy * Tx;
                     float t[PG];
                     #pragma unroll
                     for (int k = 0; k < PG; ++k)
