@@ -429,7 +429,7 @@ void launch_virial_finalize(const double* near_w, int nwarps, const double* dots
 /* ------------------------------------------------------------------ gather */
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 2) k_gather(const float4* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start,
                                                         const int* __restrict__ perm,
                                                         const float4* __restrict__ near_out,
