@@ -332,6 +332,33 @@ def test_repeatable(torch_cuda, name, r_c):
 
 
 @pytest.mark.parametrize("conv", [0, 2])
+def test_streams_and_concurrent_contexts(torch_cuda, conv):
+    # the evaluation forks its far part onto the context's own stream and joins it back: on a caller stream that
+    # is not the default one, and with two contexts evaluating at once on two streams, every result is the same,
+    # bit for bit, as one evaluation alone on the default stream
+    torch = torch_cuda
+    w = workload("water_20k")
+    x = torch.from_numpy(w.xyzq).cuda()
+    ref_ctx = usr.USeries(w.box, w.grid, 9.0, "C1_B2", max_atoms=w.n, conv=conv)
+    o_ref, e_ref = ref_ctx.eval(x)
+    torch.cuda.synchronize()
+    o_ref, e_ref = o_ref.cpu().numpy(), e_ref.cpu().numpy()
+    ctxs = [usr.USeries(w.box, w.grid, 9.0, "C1_B2", max_atoms=w.n, conv=conv) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    outs = []
+    for _ in range(3):
+        for c, s in zip(ctxs, streams):
+            with torch.cuda.stream(s):
+                outs.append(c.eval(x, stream=s.cuda_stream))
+    torch.cuda.synchronize()
+    for o, e in outs:
+        assert np.array_equal(o.cpu().numpy(), o_ref)
+        assert np.array_equal(e.cpu().numpy(), e_ref)
+    for c in ctxs + [ref_ctx]:
+        c.close()
+
+
+@pytest.mark.parametrize("conv", [0, 2])
 def test_cuda_graph_capture_and_replay(torch_cuda, conv):
     # usr_eval enqueues kernels and copies only (no allocation, no host
     # synchronisation), so it can be captured in a CUDA graph and replayed;
