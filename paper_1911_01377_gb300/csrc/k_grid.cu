@@ -19,10 +19,11 @@
  *            order, and subtracts the grid mean.
  *   gather   phi_far,i = sum_g w(g - r_i) psi_g and F_far,i = -q_i grad phi_far,i
  *            (the second spreading Gaussian of Eq. 32's 1/|S(k)|^2).  The CTA
- *            stages its psi tile in shared memory; one warp per atom contracts
- *            the stencil separably (z first, per (x, y) column), adds the near
- *            part and the self term -F(0) q_i, writes (F, phi) in caller order
- *            and reduces E = 1/2 sum q_i phi_i and its parts in FP64.
+ *            stages its psi tile in shared memory; a quad of lanes per atom
+ *            contracts the stencil separably (z first, per (x, y) column), adds
+ *            the near part and the self term -F(0) q_i, writes (F, phi) in
+ *            caller order and reduces E = 1/2 sum q_i phi_i and its parts
+ *            (compensated FP32 within a thread, FP64 across threads and blocks).
  */
 #include <cuda_bf16.h>
 

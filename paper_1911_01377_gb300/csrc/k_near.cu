@@ -5,15 +5,16 @@
  * over all j != i and periodic images.
  *
  * Cluster-pair scheme: each cell's atoms come in 8-atom spatial clusters
- * (k_cell_build).  One warp owns one i-cluster; lanes are (i = lane / 4,
- * j = lane % 4), so a warp step evaluates an 8 x 4 block of pairs with every
- * lane on the same path.  The warp walks the j-clusters of the 27 neighbour
- * cells (edge >= r_c, >= 3 per axis, so every image appears once), tests 32
- * candidate bounding boxes at a time against its own box (a conservative
- * test: it uses the same rounding as the pair distance, so it never drops a
- * pair the single-precision predicate accepts) and runs the surviving
- * cluster pairs as two 8 x 4 steps.  Every pair is evaluated from both ends,
- * so i-forces stay in registers: no atomics, a fixed order, one write per atom.
+ * (k_cell_build).  One warp owns one i-cluster; lane (i = lane / 4, g =
+ * lane % 4) takes the j atoms g and g + 4 of each j cluster in two-wide FP32,
+ * so a warp step evaluates an 8 x 8 cluster pair with every lane on the same
+ * path.  The warp walks the j-clusters of the 27 neighbour cells (edge >= r_c,
+ * >= 3 per axis, so every image appears once), tests 32 candidate bounding
+ * boxes at a time against its own box (a conservative test: it uses the same
+ * rounding as the pair distance, so it never drops a pair the single-precision
+ * predicate accepts) and runs one step per surviving cluster pair.  Every pair
+ * is evaluated from both ends, so i-forces stay in registers: no atomics, a
+ * fixed order, one write per atom.
  *
  * Per pair: r^2 by the single-precision predicate fmaf(dz,dz,fmaf(dy,dy,dx*dx));
  * 1/r by rsqrt plus one Newton step; F(u = r^2) = explicit narrow Gaussians
