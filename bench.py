@@ -10,7 +10,7 @@ The timed form is the one chosen for the benchmark's accuracy bound (rms
 relative force error <= 1e-4): per-axis convolutions as BF16x3 tensor-core
 GEMMs, spreading with the paper's GSE-style parameters (sigma_s = 0.83 h, an
 8-point stencil).  Its error against the FP64 oracle is measured in the same
-run at r_c = 8 and 13 A, and two plain FP32 forms are timed beside it: FP32
+run at r_c = 8, 10 and 13 A, and two plain FP32 forms are timed beside it: FP32
 CUDA-core convolutions with the same spreading, and the tight FP32 form
 (12-point stencil, sigma_s = h) used for the 1e-5 parity tests.
 
