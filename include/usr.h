@@ -199,8 +199,11 @@ usr_status usr_eval_host_async(usr_ctx* ctx, int n, const float* xyzq, float* ou
 
 /*
  * Synchronise the context's last stream and return the device status of the
- * evaluations since the previous call (USR_OK, USR_ERR_NONFINITE or
- * USR_ERR_INTERNAL), then clear it.
+ * evaluations since the previous call, then clear it: USR_OK;
+ * USR_ERR_NONFINITE (a non-finite position or charge); USR_ERR_TIMEOUT (a
+ * bounded wait of the tensor-core convolution ran out and the pass returned
+ * early, its output is not valid); USR_ERR_INTERNAL (a kernel's own
+ * consistency check failed).  When several are set, that order decides.
  */
 usr_status usr_last_device_status(usr_ctx* ctx);
 
@@ -301,8 +304,13 @@ usr_status usr_debug_pairs(usr_ctx* ctx, int n, const float* xyzq, int* count, u
  * last call's contents; each call clears what must start at zero on its own
  * stream, and calls that overlap on the GPU (unordered streams) race on it.
  * Non-finite rows go to cell 0 as in usr_eval but are not reported.
- * USR_ERR_CAPACITY beyond the limits above, USR_ERR_ARG for bad pointers or
- * sizes.  Enqueued on `stream`; no host synchronisation.
+ * Cost: each cell is sorted by counting, quadratic in its occupancy, so cell
+ * edges should be about the cutoff (tens to hundreds of atoms per cell); a
+ * mean occupancy above 2,048 atoms per cell is refused.
+ * USR_ERR_CAPACITY beyond the limits above (every factor of cells is checked
+ * on its own, so no product overflows), USR_ERR_ARG for bad pointers or
+ * sizes.  Enqueued on `stream`; no host synchronisation.  n = 0 writes
+ * cell_start as all zeros.
  */
 usr_status usr_cells_static(int n, const float* xyzq, const double* box, const int* cells, int* cell, int* perm,
                             int* cell_start, float* xw, void* stream);

@@ -264,16 +264,21 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
     }
 }
 
-void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
-                cudaStream_t st)
+cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                       float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
+                       int* status, cudaStream_t st)
 {
-    cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
+    if (e != cudaSuccess) return e;
     int nb = (n + 255) / 256;
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cell_sort<<<ncell, kSortThreads, 0, st>>>(cell_start, unsorted, wpos, perm, spos);
+    return cudaGetLastError();
 }
 
 /* The pair kernel's full cell list: counts, scan, placement, then the sort and the clusters fused per cell. */

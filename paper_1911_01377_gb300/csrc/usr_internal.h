@@ -168,9 +168,9 @@ struct ConvTcMaps {
 };
 
 // ---- launchers (all enqueue on `st`) ----
-void launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos, int* status,
-                cudaStream_t st);
+cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                       float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
+                       int* status, cudaStream_t st);
 void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                       float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
                       float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, int* status, cudaStream_t st);

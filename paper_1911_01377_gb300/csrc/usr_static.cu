@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kStaticMaxAtoms = 1 << 18;     // 262,144 atoms
 constexpr int kStaticMaxCells = 1 << 16;     // 65,536 cells
+constexpr long long kStaticMaxPerCell = 2048;   // mean atoms per cell (the per-cell sort's shared-memory size)
 constexpr int kMaxDevices = 64;
 
 /* Layout of the scratch array (byte offsets, each 256-byte aligned). */
@@ -81,9 +82,15 @@ extern "C" usr_status usr_cells_static(int n, const float* xyzq, const double* b
     long long ncell = 1;
     for (int a = 0; a < 3; ++a) {
         if (!(box[a] > 0.0) || !(box[a] < 1e30) || cells[a] < 1) return USR_ERR_ARG;
+        // each factor is checked before it is multiplied in, so the product (at most 2^32) cannot overflow
+        if (cells[a] > kStaticMaxCells) return USR_ERR_CAPACITY;
         ncell *= cells[a];
+        if (ncell > kStaticMaxCells) return USR_ERR_CAPACITY;
     }
-    if (n > kStaticMaxAtoms || ncell > kStaticMaxCells) return USR_ERR_CAPACITY;
+    if (n > kStaticMaxAtoms) return USR_ERR_CAPACITY;
+    // the per-cell sort is quadratic in a cell's occupancy: refuse calls whose mean occupancy already
+    // exceeds what one cell's shared-memory sort holds
+    if (n > kStaticMaxPerCell * ncell) return USR_ERR_CAPACITY;
     if (!cell_start) return USR_ERR_ARG;
     if (n > 0 && (!xyzq || !aligned16(xyzq) || !cell || !perm || !xw || !aligned16(xw))) return USR_ERR_ARG;
     for (int a = 0; a < 3; ++a) {
@@ -94,6 +101,8 @@ extern "C" usr_status usr_cells_static(int n, const float* xyzq, const double* b
         b.nc[a] = cells[a];
         b.n[a] = 1;
     }
+    // a launch error left by earlier, unrelated work on this thread must not be reported as this call's
+    cudaGetLastError();
     unsigned char* base = nullptr;
     usr_status s = scratch_address(&base);
     if (s != USR_OK) return s;
@@ -110,8 +119,10 @@ extern "C" usr_status usr_cells_static(int n, const float* xyzq, const double* b
         return USR_OK;
     }
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return USR_ERR_CUDA;
-    // launch_bin clears the per-cell counters on `st` before counting
-    usr::launch_bin(n, reinterpret_cast<const float4*>(xyzq), b, (int)ncell, count, cell, slot, wpos, cell_start,
-                    pstart, unsorted, perm, reinterpret_cast<float4*>(xw), status, st);
-    return cudaGetLastError() == cudaSuccess ? USR_OK : USR_ERR_CUDA;
+    // launch_bin clears the per-cell counters on `st` before counting and returns the first error of its
+    // memset and launches
+    const cudaError_t e = usr::launch_bin(n, reinterpret_cast<const float4*>(xyzq), b, (int)ncell, count, cell, slot,
+                                          wpos, cell_start, pstart, unsorted, perm, reinterpret_cast<float4*>(xw),
+                                          status, st);
+    return e == cudaSuccess ? USR_OK : USR_ERR_CUDA;
 }

@@ -288,7 +288,7 @@ class USeries:
         usr_virial(self.ctx, W.data_ptr())
         return W.view(3, 3)
 
-    def debug_cells(self, xyzq):
+    def debug_cells(self, xyzq, stream=None):
         import torch
         n = xyzq.shape[0]
         ncell = self.info.cells[0] * self.info.cells[1] * self.info.cells[2]
@@ -298,7 +298,7 @@ class USeries:
         start = torch.empty(ncell + 1, dtype=torch.int32, device=dev)
         xw = torch.empty((n, 4), dtype=torch.float32, device=dev)
         usr_debug_cells(self.ctx, n, xyzq.data_ptr(), cell.data_ptr(), perm.data_ptr(), start.data_ptr(),
-                        xw.data_ptr())
+                        xw.data_ptr(), stream)
         return cell, perm, start, xw
 
     def debug_pairs(self, xyzq):

@@ -97,3 +97,15 @@ def test_init_without_gpu_fails_cleanly(libusr):
     with pytest.raises(usr.UsrError) as e:
         usr.usr_init(usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=100))
     assert e.value.code in (4, 5)
+
+
+def test_static_cell_list_refuses_oversized_cell_counts(libusr):
+    """usr_cells_static checks every cell factor before multiplying, so a product that would overflow
+    64 bits is refused as a capacity error before any device call (null buffers: nothing is touched)."""
+    for cells in [(2_097_152, 2_097_152, 2_097_152), (65_537, 1, 1), (256, 256, 2), (1 << 30, 1 << 30, 4)]:
+        with pytest.raises(usr.UsrError) as e:
+            usr.usr_cells_static(4, None, (10.0, 10.0, 10.0), cells, None, None, None, None, 0)
+        assert e.value.code == 7
+    with pytest.raises(usr.UsrError) as e:          # mean occupancy above 2,048 atoms per cell
+        usr.usr_cells_static(2049 * 27, None, (10.0, 10.0, 10.0), (3, 3, 3), None, None, None, None, 0)
+    assert e.value.code == 7

@@ -32,16 +32,16 @@ def torch_cuda():
     return torch
 
 
-def _static_cells(torch, xyzq, box, cells):
+def _static_cells(torch, xyzq, box, cells, stream=None):
     n = xyzq.shape[0]
     ncell = int(np.prod(cells))
-    cell = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-    perm = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    cell = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    perm = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
     start = torch.full((ncell + 1,), -7, dtype=torch.int32, device="cuda")
-    xw = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    xw = torch.full((max(n, 1), 4), float("nan"), dtype=torch.float32, device="cuda")
     usr.usr_cells_static(n, xyzq.data_ptr(), box, cells, cell.data_ptr(), perm.data_ptr(), start.data_ptr(),
-                         xw.data_ptr())
-    return cell, perm, start, xw
+                         xw.data_ptr(), stream)
+    return cell[:n], perm[:n], start, xw[:n]
 
 
 def _same(torch, a, b):
@@ -76,3 +76,24 @@ def test_static_cell_list_limits(torch_cuda):
         usr.usr_cells_static(4, x.data_ptr(), (10.0, 10.0, 10.0), (64, 64, 17), x.data_ptr(), x.data_ptr(),
                              x.data_ptr(), x.data_ptr())
     assert e.value.code == 7
+
+
+def test_static_cell_list_on_a_side_stream_and_empty(torch_cuda):
+    """A call enqueued on a non-default stream gives the same list as the context entry point on that
+    stream; n = 0 writes cell_start as all zeros."""
+    torch = torch_cuda
+    w = W.get("water_3k")
+    ctx = usr.USeries(w.box, w.grid, 9.0, "C1_B2", max_atoms=w.n)
+    cells = list(ctx.info.cells)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        x = torch.from_numpy(w.xyzq).cuda()
+        ref = ctx.debug_cells(x, stream=s)
+        got = _static_cells(torch, x, w.box, cells, stream=s.cuda_stream)
+    s.synchronize()
+    _same(torch, got, ref)
+    ctx.close()
+    empty = torch.zeros((1, 4), dtype=torch.float32, device="cuda")
+    _, _, start, _ = _static_cells(torch, empty[:0], w.box, cells)
+    torch.cuda.synchronize()
+    assert np.array_equal(start.cpu().numpy(), np.zeros(int(np.prod(cells)) + 1, dtype=np.int32))
