@@ -5,6 +5,9 @@ One step = one evaluation of the 63,996-charge membrane slab (80 x 80 x 100 A,
 r_c = 8, 9, 10, 11, 12, 13 A, inputs resident in HBM.  value = atom-evals/s
 (charges x evaluations / second; device time from CUDA events on the
 evaluation stream; L2 flushed between steps by writing a 512 MB buffer).
+e2e = the same metric through the host-buffer entry point (pinned host
+buffers, copies and the synchronisation inside the timed region, L2 flushed
+before every step, CUDA events around each step).
 
 The timed form is the one chosen for the benchmark's accuracy bound (rms
 relative force error <= 1e-4): per-axis convolutions as BF16x3 tensor-core
@@ -12,14 +15,17 @@ GEMMs, spreading with the paper's GSE-style parameters (sigma_s = 0.83 h, an
 8-point stencil).  Its error against the FP64 oracle is measured in the same
 run at r_c = 8, 10 and 13 A, and two plain FP32 forms are timed beside it: FP32
 CUDA-core convolutions with the same spreading, and the tight FP32 form
-(12-point stencil, sigma_s = h) used for the 1e-5 parity tests.
+(12-point stencil, sigma_s = h) used for the 1e-5 parity tests.  The
+1,064,799-charge water box (r_c = 10 A, 176^3 grid) is timed in four forms as
+well, and the serving stream of 512 independent systems.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--serve-systems M] [--scale]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--serve-systems M] [--no-scale]
 
 N > 1 (under torch.distributed.run): every rank evaluates its own replica of
 the workload (independent systems, no collective), value sums all ranks over
 the slowest rank's time.  --impl reference times the FP64 oracle on the host
-cores instead (the reference arm).
+cores instead (the reference arm): one full evaluation of the slab per step,
+the same definition as the cpu_baseline of the GPU arm.
 """
 from __future__ import annotations
 
@@ -43,11 +49,13 @@ SWEEP = (8.0, 9.0, 10.0, 11.0, 12.0, 13.0)
 # kernels of one evaluation: bin_count, scan, place, cell_build, near, spread, tile_reduce, conv x, conv y,
 # conv z, grid_mean, gather
 KERNELS_PER_EVAL = 12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock
+# algorithmic flops of one unordered pair inside r_c (the survey's 30-50 flop estimate of the pair
+# arithmetic, its midpoint), the unit of the pair kernel's roofline
+NEAR_FLOPS_PER_PAIR = 40
 # DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over the evaluation
-# launches of one ncu capture of `bench.py --steps 2 --warmup 3 --serve-systems 0`; None whenever the
-# pair kernel has changed since that capture
-NEAR_TRAFFIC_BYTES = 1.643e6
+# launches of one ncu capture; None whenever the pair kernel has changed since that capture
+NEAR_TRAFFIC_BYTES = None
 # forms: (name, conv, spread_points, spread_sigma_over_h)
 CHOSEN = ("bf16x3_gse8", 2, 8, 0.83)
 COMPARATORS = (("fp32_gse8", 0, 8, 0.83), ("fp32_tight12", 0, 12, 1.0))
@@ -73,11 +81,11 @@ def stage_floors(n, pairs, info, grid, spread_points, hilo_products, peaks):
     HBM peak (4 G in and 4 N G out on x, 4 N G both ways on y, 4 N G in and 4 G out on z)."""
     G = grid[0] * grid[1] * grid[2]
     N = info.n_terms
-    fp32 = FP32_PEAK_TFLOPS * 1e12
+    fp32 = peaks["fp32_tflops"] * 1e12
     hbm = peaks["hbm_gbs"] * 1e9
     tc = peaks["bf16_tflops"] * 1e12
     f = {"bin": 60.0 * n / hbm,
-         "near": pairs * near_flops_per_pair(info.poly_degree, info.n_explicit) / fp32,
+         "near": pairs * NEAR_FLOPS_PER_PAIR / fp32,
          "spread": 2.0 * spread_points ** 3 * n / fp32,
          "gather": 8.0 * spread_points ** 3 * n / fp32}
     byts = {"conv_x": 4.0 * G + 4.0 * N * G, "conv_y": 8.0 * N * G, "conv_z": 4.0 * N * G + 4.0 * G}
@@ -87,7 +95,7 @@ def stage_floors(n, pairs, info, grid, spread_points, hilo_products, peaks):
 
 
 def near_flops_per_pair(poly_degree: int, n_explicit: int) -> int:
-    """Algorithmic flops of one pair inside r_c, counted once per unordered pair (FMA = 2):
+    """The pair kernel's own arithmetic for one pair inside r_c, counted once per unordered pair (FMA = 2):
     displacement 3, r^2 5, rsqrt + Newton step 5, polynomial argument 2, Horner value and
     derivative 4 D, derivative scale 1, 1/r^3 2, force scale 3, forces on both atoms 12,
     potentials of both atoms 5; each explicit Gaussian adds exp (counted 8) + 5."""
@@ -182,29 +190,26 @@ def cpu_oracle_eval(w, r_c, targets=None):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    """Reference arm: the FP64 oracle on the host cores, one full evaluation (energy, every force and
+    potential) of the slab per step, the cutoff cycling through the sweep."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np
     import oracle as O
     from paper_1911_01377_gb300 import workloads as W
     w = W.get(WORKLOAD)
-    rng = np.random.default_rng(7)
-    n_t = 2048
     times = []
     for step in range(args.warmup + args.steps):
         r_c = SWEEP[step % len(SWEEP)]
-        targets = rng.choice(w.n, size=n_t, replace=False)
         t0 = time.perf_counter()
-        cpu_oracle_eval(w, r_c, targets=targets)
+        cpu_oracle_eval(w, r_c)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
     total = sum(times)
-    value = n_t * len(times) / total
-    sample = (f"FP64 oracle (direct near sum + exact k-space far sum) on all {w.n} charges, "
-              f"forces+potentials for {n_t} random target atoms per step, r_c cycling {SWEEP[0]:g}-{SWEEP[-1]:g} A")
+    value = w.n * len(times) / total
+    sample = (f"one full FP64 oracle evaluation (direct near sum + exact k-space far sum; energy, all forces and "
+              f"potentials) of the {w.n}-charge slab per step, r_c cycling {SWEEP[0]:g}-{SWEEP[-1]:g} A")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -398,20 +403,27 @@ def run_gpu(args):
     evals = n * len(SWEEP) * args.steps * ws
     value = whole_job_rate(n * len(SWEEP) * args.steps, ws, total_ms / 1e3)
 
-    # end to end through the host-buffer entry point (pinned memory, copies inside the timed region)
+    # end to end through the host-buffer entry point (pinned memory, copies inside the timed region), under
+    # the same protocol as `value`: L2 flushed before every step, CUDA events around the step's six calls
     xh = torch.from_numpy(w.xyzq).pin_memory()
     oh = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in SWEEP]
     eh = [torch.empty(4, dtype=torch.float64).pin_memory() for _ in SWEEP]
     for _ in range(max(1, args.warmup)):
+        flush.fill_(1.0)
         for c, o, e in zip(ctxs, oh, eh):
             usr.usr_eval_host(c.ctx, n, xh.data_ptr(), o.data_ptr(), e.data_ptr(), stream)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    t_e2e = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k % 7))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for c, o, e in zip(ctxs, oh, eh):
             usr.usr_eval_host(c.ctx, n, xh.data_ptr(), o.data_ptr(), e.data_ptr(), stream)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1) / 1e3
     t_e2e = max_over_ranks(t_e2e, dev)
     e2e_value = whole_job_rate(n * len(SWEEP) * args.steps, ws, t_e2e)
     chosen_outs = [o.double().cpu().numpy() for o in outs]
@@ -430,30 +442,38 @@ def run_gpu(args):
             c.close()
 
     serving = run_serving(usr, torch, args.serve_systems) if args.serve_systems > 0 else None
-    scale = run_scale(usr, torch, args.steps, args.warmup, flush, stream) if args.scale else None
+    scale = run_scale(usr, torch, args.steps, args.warmup, flush, stream) if not args.no_scale else None
+    fp32_peak = usr.usr_fp32_peak()     # measured FP32 FMA peak of this GPU (the pair kernel's denominator)
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    # dominant kernel and its roofline (stage times are CUDA events on the evaluation stream)
+    # the dominant kernel (the pair kernel) and its roofline: its launch duration is the near stage's CUDA-event
+    # time on the evaluation stream (events just before and after its launch), averaged over the timed steps
     per_stage = [sum(stage_ms[k][s] for k in range(len(SWEEP))) / (len(SWEEP) * args.steps)
                  for s in range(usr.USR_NSTAGES)]
-    dom = max(range(usr.USR_NSTAGES), key=lambda s: per_stage[s])
-    roof = None
-    if usr.STAGES[dom] == "near":
-        flops = sum(p * near_flops_per_pair(i.poly_degree, i.n_explicit) for p, i in zip(pairs, infos))
-        t_dom = sum(stage_ms[k][dom] for k in range(len(SWEEP))) / args.steps / 1e3
-        achieved = flops / t_dom / 1e12
-        roof = {"kernel": "near (k_near_cl)", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NEAR_TRAFFIC_BYTES,
-                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz maximum SM clock",
-                "flops_per_pair": [near_flops_per_pair(i.poly_degree, i.n_explicit) for i in infos],
-                "pairs_per_eval": pairs}
+    dom = usr.STAGES.index("near")
+    flops = sum(p * NEAR_FLOPS_PER_PAIR for p in pairs)                      # one launch per cutoff
+    t_dom = sum(stage_ms[k][dom] for k in range(len(SWEEP))) / args.steps / 1e3
+    achieved = flops / t_dom / 1e12
+    peak_ok = fp32_peak > 0.0
+    peak = fp32_peak if peak_ok else FP32_PEAK_DERIVED_TFLOPS
+    roof = {"kernel": "near (k_near_half)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": NEAR_TRAFFIC_BYTES,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+            "peak_source": ("measured: register-only two-wide FFMA loop over all SMs (usr_fp32_peak), this run"
+                            if peak_ok else "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"),
+            "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
+            "flops_per_pair": NEAR_FLOPS_PER_PAIR,
+            "flops_per_pair_note": "algorithmic: the survey's 30-50 flops per pair inside r_c, midpoint; the kernel's "
+                                   "own arithmetic is " + ", ".join(str(near_flops_per_pair(i.poly_degree, i.n_explicit))
+                                                                    for i in infos[:1]) + " per pair",
+            "pairs_per_eval": pairs, "launch_ms_mean": 1e3 * t_dom / len(SWEEP)}
 
     # stage-wise floors of the chosen form, summed over the sweep, against the measured stage times
     peaks = measured_peaks()
+    peaks["fp32_tflops"] = peak
     floors = [stage_floors(n, p, i, w.grid, CHOSEN[2], 3, peaks) for p, i in zip(pairs, infos)]
     floor_ms = {st: sum(fl[st] for fl in floors) / len(SWEEP) for st in usr.STAGES}
     eval_ms = total_ms / args.steps / len(SWEEP)
@@ -462,9 +482,10 @@ def run_gpu(args):
                   "frac_of_eval_time": sum(floor_ms.values()) / eval_ms,
                   "note": "the far stages run concurrently with the near stage (two streams), so the measured "
                           "stages add up to more than an evaluation; frac = sum of the floors / evaluation time",
-                  "peaks": {"fp32_tflops": FP32_PEAK_TFLOPS, "hbm_gbs": peaks["hbm_gbs"],
+                  "peaks": {"fp32_tflops": peak, "hbm_gbs": peaks["hbm_gbs"],
                             "bf16_tflops": peaks["bf16_tflops"],
-                            "source": f"FP32 derived; HBM and BF16 {peaks['source']} (MEASURED_PEAKS.json)"}}
+                            "source": f"FP32 {'measured in this run' if peak_ok else 'derived'}; HBM and BF16 "
+                                      f"{peaks['source']} (MEASURED_PEAKS.json)"}}
 
     # accuracy of every form against the FP64 oracle at r_c = 8 and of the chosen form at 10 and 13 (full evaluations)
     t0 = time.perf_counter()
@@ -524,8 +545,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--serve-systems", type=int, default=512,
                     help="systems in the serving stream (0 skips the serving measurement)")
-    ap.add_argument("--scale", action="store_true",
-                    help="also time the 1,064,799-charge water box (r_c = 10 A, 176^3 grid) in every form")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 1,064,799-charge water box (r_c = 10 A, 176^3 grid, every form)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -358,6 +358,15 @@ usr_status usr_set_profiling(usr_ctx* ctx, int on);
  */
 usr_status usr_stage_times(usr_ctx* ctx, float* ms);
 
+/*
+ * FP32 fused multiply-add throughput of the current device in TFLOP/s,
+ * measured with a register-only loop of two-wide FMAs over every SM (CUDA
+ * events around one launch after a warm-up launch; synchronises, allocates a
+ * small scratch buffer).  The paper has no counterpart: this is the measured
+ * peak that the pair kernel's FP32 roofline fraction divides by.
+ */
+usr_status usr_fp32_peak(double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,50 +61,74 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
 }
 
 /*
- * Exclusive scans of count[0..ncell) into start[0..ncell] and of the counts
- * rounded up to a multiple of 8 into pstart[0..ncell] (the padded 8-atom
- * cluster layout of the pair kernel), one block of 1024 threads.
+ * Exclusive scans, one block of 1024 threads: of count[0..ncell) into
+ * start[0..ncell] and of the counts rounded up to a multiple of 8 into
+ * pstart[0..ncell] (the padded 8-atom cluster layout of the pair kernels).
+ * With gfull given, also the half-list pair kernel's groups of gcl
+ * consecutive clusters of one cell: the full groups per cell into
+ * gfull[0..ncell], the one partial group a cell may end with into
+ * gpart[0..ncell]; and the kernel's work-queue counter is set to zero.
  */
 __global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict__ count, int* __restrict__ start,
-                                               int* __restrict__ pstart)
+                                               int* __restrict__ pstart, int* __restrict__ gfull,
+                                               int* __restrict__ gpart, int gcl, int* __restrict__ queue)
 {
-    __shared__ int2 warp_sums[32];
-    __shared__ int2 carry;
-    if (threadIdx.x == 0) carry = make_int2(0, 0);
+    __shared__ int4 warp_sums[32];
+    __shared__ int4 carry;
+    if (threadIdx.x == 0) {
+        carry = make_int4(0, 0, 0, 0);
+        if (queue) *queue = 0;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int base = 0; base < ncell; base += 1024) {
-        int i = base + threadIdx.x;
-        int v = i < ncell ? count[i] : 0;
-        int vp = (v + 7) & ~7;
-        int x = v, xp = vp;
+        const int i = base + threadIdx.x;
+        const int v = i < ncell ? count[i] : 0;
+        const int vp = (v + 7) & ~7;
+        const int vf = (vp >> 3) / gcl, vq = (vp >> 3) % gcl != 0 ? 1 : 0;
+        int4 x = make_int4(v, vp, vf, vq);
         #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            int yp = __shfl_up_sync(0xffffffffu, xp, o);
-            if (lane >= o) { x += y; xp += yp; }
+            const int4 y = make_int4(__shfl_up_sync(0xffffffffu, x.x, o), __shfl_up_sync(0xffffffffu, x.y, o),
+                                     __shfl_up_sync(0xffffffffu, x.z, o), __shfl_up_sync(0xffffffffu, x.w, o));
+            if (lane >= o) { x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w; }
         }
-        if (lane == 31) warp_sums[wid] = make_int2(x, xp);
+        if (lane == 31) warp_sums[wid] = x;
         __syncthreads();
         if (wid == 0) {
-            int2 w = warp_sums[lane];
+            int4 w = warp_sums[lane];
             #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, w.x, o);
-                int yp = __shfl_up_sync(0xffffffffu, w.y, o);
-                if (lane >= o) { w.x += y; w.y += yp; }
+                const int4 y = make_int4(__shfl_up_sync(0xffffffffu, w.x, o), __shfl_up_sync(0xffffffffu, w.y, o),
+                                         __shfl_up_sync(0xffffffffu, w.z, o), __shfl_up_sync(0xffffffffu, w.w, o));
+                if (lane >= o) { w.x += y.x; w.y += y.y; w.z += y.z; w.w += y.w; }
             }
             warp_sums[lane] = w;   // inclusive
         }
         __syncthreads();
-        int2 pre = wid > 0 ? warp_sums[wid - 1] : make_int2(0, 0);
-        int incl = x + pre.x + carry.x, inclp = xp + pre.y + carry.y;
-        if (i < ncell) { start[i] = incl - v; pstart[i] = inclp - vp; }
+        const int4 pre = wid > 0 ? warp_sums[wid - 1] : make_int4(0, 0, 0, 0);
+        const int4 incl = make_int4(x.x + pre.x + carry.x, x.y + pre.y + carry.y, x.z + pre.z + carry.z,
+                                    x.w + pre.w + carry.w);
+        if (i < ncell) {
+            start[i] = incl.x - v;
+            pstart[i] = incl.y - vp;
+            if (gfull) {
+                gfull[i] = incl.z - vf;
+                gpart[i] = incl.w - vq;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = make_int2(incl, inclp);
+        if (threadIdx.x == 1023) carry = incl;
         __syncthreads();
     }
-    if (threadIdx.x == 0) { start[ncell] = carry.x; pstart[ncell] = carry.y; }
+    if (threadIdx.x == 0) {
+        start[ncell] = carry.x;
+        pstart[ncell] = carry.y;
+        if (gfull) {
+            gfull[ncell] = carry.z;
+            gpart[ncell] = carry.w;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
@@ -192,16 +216,22 @@ __device__ __forceinline__ int morton_key(float4 p, float ox, float oy, float oz
 /*
  * The cell sort and the clusters in one pass, one CTA per cell: first the
  * cell's atoms in caller-index order (perm, sorted rows) with the Morton key
- * of each sorted row, then the cluster order from the keys (as above).
+ * of each sorted row, then the cluster order from the keys (as above).  Also
+ * the first cluster of each of the cell's groups of gcl clusters, and the
+ * cell's rows of the pair kernel's fixed-point accumulators set to zero.
  */
 __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restrict__ start,
                                                              const int* __restrict__ pstart,
+                                                             const int* __restrict__ gfull,
+                                                             const int* __restrict__ gpart, int gcl,
                                                              const int* __restrict__ unsorted,
                                                              const float4* __restrict__ wpos, BoxF b,
                                                              int* __restrict__ perm, float4* __restrict__ spos,
                                                              int* __restrict__ key, float4* __restrict__ cpos,
                                                              int* __restrict__ cidx, int* __restrict__ ccell,
-                                                             float4* __restrict__ bblo, float4* __restrict__ bbhi)
+                                                             float4* __restrict__ bblo, float4* __restrict__ bbhi,
+                                                             int* __restrict__ gfirst,
+                                                             unsigned long long* __restrict__ acc)
 {
     __shared__ int v[kSortMax];
     __shared__ int ks[kSortMax];
@@ -214,6 +244,15 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
     const float kx = 8.0f * b.cs[0], ky = 8.0f * b.cs[1], kz = 8.0f * b.cs[2];
     const bool in_smem = m <= kSortMax;
     float* cp = reinterpret_cast<float*>(cpos);
+    {
+        // full groups in cell order, then the partial ones (the pair kernel takes them in that order,
+        // so its last work units are the small ones)
+        const int f0 = gfull[c], nf = gfull[c + 1] - f0;
+        for (int k = threadIdx.x; k < nf; k += kSortThreads) gfirst[f0 + k] = (p0 >> 3) + k * gcl;
+        if (threadIdx.x == 0 && gpart[c + 1] > gpart[c]) gfirst[gfull[b.nc[0] * b.nc[1] * b.nc[2]] + gpart[c]] = (p0 >> 3) + nf * gcl;
+        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc + 4 * (size_t)s0);
+        for (int e = threadIdx.x; e < 2 * m; e += kSortThreads) a2[e] = make_ulonglong2(0ull, 0ull);
+    }
     if (in_smem)
         for (int e = threadIdx.x; e < m; e += kSortThreads) v[e] = unsorted[s0 + e];
     __syncthreads();
@@ -273,7 +312,7 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
     int nb = (n + 255) / 256;
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
+    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, nullptr, nullptr, 1, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -281,19 +320,21 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
     return cudaGetLastError();
 }
 
-/* The pair kernel's full cell list: counts, scan, placement, then the sort and the clusters fused per cell. */
+/* The pair kernels' full cell list: counts, scan, placement, then the sort and the clusters fused per cell. */
 void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                      float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
-                      float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, int* status, cudaStream_t st)
+                      float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
+                      int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
+                      float4* bbhi, unsigned long long* near_acc, int* status, cudaStream_t st)
 {
+    const int gcl = near_group_clusters();
     cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
     int nb = (n + 255) / 256;
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
-    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart);
+    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, gfull, gpart, gcl, queue);
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
     // slot[] is free after placement: it holds the Morton keys of cells too large for shared memory
-    k_cell_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, unsorted, wpos, b, perm, spos, slot, cpos, cidx,
-                                                  ccell, bblo, bbhi);
+    k_cell_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, gfull, gpart, gcl, unsorted, wpos, b, perm, spos,
+                                                  slot, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc);
 }
 
 }  // namespace usr

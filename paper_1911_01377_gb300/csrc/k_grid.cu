@@ -404,15 +404,18 @@ void launch_grid_dot(const GridArgs& g, const float* a, const float* b, double s
 }
 
 /*
- * W = W_near + delta E_far + 1/2 <rho, psi_ab>: near from per-warp slots (in
- * warp order), far from the six grid dot products (already halved) and E_far.
+ * W = W_near + delta E_far + 1/2 <rho, psi_ab>: near from the pair kernel's per-unit slots (in unit
+ * order; the unit count follows from the group totals of the cell list), far from the six grid dot
+ * products (already halved) and E_far.
  */
-__global__ void k_virial_finalize(const double* __restrict__ near_w, int nwarps, const double* __restrict__ dots,
-                                  const double* __restrict__ energy, double* __restrict__ W)
+__global__ void k_virial_finalize(const double* __restrict__ near_w, ClusterList L, int ncell, int nsplit,
+                                  const double* __restrict__ dots, const double* __restrict__ energy,
+                                  double* __restrict__ W)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int units = nsplit * (L.gfull[ncell] + L.gpart[ncell]);
     double wn[6] = {0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < nwarps; ++w)
+    for (int w = 0; w < units; ++w)
         for (int c = 0; c < 6; ++c) wn[c] += near_w[6 * w + c];
     const double ef = energy[2];
     double t[6];
@@ -421,19 +424,29 @@ __global__ void k_virial_finalize(const double* __restrict__ near_w, int nwarps,
     for (int e = 0; e < 9; ++e) W[e] = t[map[e]];
 }
 
-void launch_virial_finalize(const double* near_w, int nwarps, const double* dots, const double* energy, double* W,
-                            cudaStream_t st)
+void launch_virial_finalize(const double* near_w, const ClusterList& L, int ncell, const double* dots,
+                            const double* energy, double* W, cudaStream_t st)
 {
-    k_virial_finalize<<<1, 32, 0, st>>>(near_w, nwarps, dots, energy, W);
+    k_virial_finalize<<<1, 32, 0, st>>>(near_w, L, ncell, near_splits(), dots, energy, W);
 }
 
 /* ------------------------------------------------------------------ gather */
+
+/* The pair kernel's near part of sorted atom s: four fixed-point sums (2^-32 units) as FP32. */
+__device__ __forceinline__ float4 near_part(const unsigned long long* __restrict__ acc, int s)
+{
+    const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(acc + 4 * (size_t)s);
+    const ulonglong2 u = a2[0], v = a2[1];
+    constexpr float k = 2.3283064365386963e-10f;   // 2^-32, exact
+    return make_float4(__ll2float_rn((long long)u.x) * k, __ll2float_rn((long long)u.y) * k,
+                       __ll2float_rn((long long)v.x) * k, __ll2float_rn((long long)v.y) * k);
+}
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start,
                                                         const int* __restrict__ perm,
-                                                        const float4* __restrict__ near_out,
+                                                        const unsigned long long* __restrict__ near_acc,
                                                         const float* __restrict__ psi, GridArgs g,
                                                         float4* __restrict__ out, float4* __restrict__ near_dbg,
                                                         float4* __restrict__ far_dbg, double* __restrict__ partial,
@@ -482,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict
         for (int a = threadIdx.x; a < nch; a += kThreads) {
             const int s = block_atom(c0 + a, rs, pre);
             sp[a] = pos[s];
-            sn[a] = near_out[s];
+            sn[a] = near_part(near_acc, s);
             si[a] = perm[s];
         }
         __syncthreads();
@@ -680,11 +693,11 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
 
 #define USR_GATHER_CASE(PP)                                                                                      \
     case PP:                                                                                                     \
-        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, perm, near_out, psi, g, out, near_dbg, far_dbg, \
+        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, perm, near_acc, psi, g, out, near_dbg, far_dbg, \
                                                   partial, counter, energy, status);                             \
         break;
 
-void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const float4* near_out,
+void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const unsigned long long* near_acc,
                    const float* psi, const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg,
                    double* partial, unsigned int* counter, double* energy, int* status, cudaStream_t st)
 {

@@ -35,10 +35,12 @@ struct usr_ctx {
     // cell list
     int *d_count = nullptr, *d_cell_of = nullptr, *d_slot = nullptr, *d_cell_start = nullptr;
     int *d_unsorted = nullptr, *d_perm = nullptr, *d_status = nullptr;
-    float4 *d_wpos = nullptr, *d_spos = nullptr, *d_near = nullptr;
+    float4 *d_wpos = nullptr, *d_spos = nullptr;
+    unsigned long long* d_nacc = nullptr;   // near part, 4 fixed-point sums per sorted atom
     // 8-atom clusters of the pair kernel (padded layout)
-    int max_clusters = 0;
-    int *d_pstart = nullptr, *d_cidx = nullptr, *d_ccell = nullptr;
+    int max_clusters = 0, max_groups = 0;
+    int *d_pstart = nullptr, *d_cidx = nullptr, *d_ccell = nullptr, *d_gfull = nullptr, *d_gpart = nullptr;
+    int *d_gfirst = nullptr, *d_queue = nullptr;
     float4 *d_cpos = nullptr, *d_bblo = nullptr, *d_bbhi = nullptr;
     // grids and convolution tables
     float *d_rho = nullptr, *d_X = nullptr, *d_Y = nullptr, *d_psi = nullptr;
@@ -109,7 +111,7 @@ void free_all(usr_ctx* c)
 {
     void* ptrs[] = {c->d_count, c->d_cell_of, c->d_slot, c->d_cell_start, c->d_unsorted, c->d_perm, c->d_status,
                     c->d_pstart, c->d_cidx, c->d_ccell, c->d_cpos, c->d_bblo, c->d_bbhi,
-                    c->d_wpos, c->d_spos, c->d_near, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
+                    c->d_wpos, c->d_spos, c->d_nacc, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
                     c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_tilebuf,
                     c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_rho_hi, c->d_rho_lo, c->d_X_hi, c->d_X_lo,
@@ -230,12 +232,14 @@ double usr::plan_device_bytes(const Plan& P)
     const double nmax = std::max(nx, std::max(ny, nz));
     double b = 4096 + 4 * (ncell + 1) * 3 + 16 * ncl * 8 + 4 * ncl * 8 + 4 * ncl + 32 * ncl;   // cells, clusters
     b += 8 * (3 * N * nmax + 4 * N);                                               // 1D kernel tables
-    b += na * (4 * 4 + 16 * 7);                                                    // per-atom arrays
+    b += na * (4 * 4 + 16 * 6 + 32);                                               // per-atom arrays
+    const double ngr = near_max_groups((int)na, (int)ncell);
+    b += 8 * (ncell + 1) + 4 * ngr + 4;                                            // pair-kernel groups
     b += 4 * G + 8 * nsb * 5 + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
     if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
-        b += 8 * G + 48 * 4 * std::ceil((na + 7 * ncell + 7) / 32) + 8 * (16 + kGridMeanBlocks);
+        b += 8 * G + 48 * near_units((int)ngr) + 8 * (16 + kGridMeanBlocks);
         if (tc) b += 4 * G * (1 + 2 * N);
     }
     if (!tc) {
@@ -279,6 +283,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int nsb = usr::tile_blocks(P.tile);
     c->max_clusters = (int)((na + 7 * (size_t)c->ncell + 7) / 8);
+    c->max_groups = usr::near_max_groups((int)na, c->ncell);
     const size_t ncl = (size_t)c->max_clusters;
     const size_t f4 = sizeof(float4), i4 = sizeof(int), fl = sizeof(float), db = sizeof(double);
 #define ENSURE(ptr, bytes) \
@@ -289,6 +294,10 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_cpos, f4 * ncl * 8);
     ENSURE(c->d_cidx, i4 * ncl * 8);
     ENSURE(c->d_ccell, i4 * ncl);
+    ENSURE(c->d_gfull, i4 * (c->ncell + 1));
+    ENSURE(c->d_gpart, i4 * (c->ncell + 1));
+    ENSURE(c->d_queue, i4);
+    ENSURE(c->d_gfirst, i4 * c->max_groups);
     ENSURE(c->d_bblo, f4 * ncl);
     ENSURE(c->d_bbhi, f4 * ncl);
     ENSURE(c->d_cell_of, i4 * na);
@@ -298,7 +307,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_status, i4);
     ENSURE(c->d_wpos, f4 * na);
     ENSURE(c->d_spos, f4 * na);
-    ENSURE(c->d_near, f4 * na);
+    ENSURE(c->d_nacc, sizeof(unsigned long long) * 4 * na);
     ENSURE(c->d_psi, fl * G);
     ENSURE(c->d_spread_partial, db * nsb);
     ENSURE(c->d_mean, db);
@@ -349,7 +358,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
         ENSURE(c->d_vktab, db * nkt * 6);
         ENSURE(c->d_psiv, fl * G);
         if (c->tc) ENSURE(c->d_rho32, fl * G);
-        ENSURE(c->d_vnear, db * 6 * usr::near_warps(c->max_clusters));
+        ENSURE(c->d_vnear, db * 6 * usr::near_units(c->max_groups));
         ENSURE(c->d_vdot, db * 6);
         ENSURE(c->d_vpart, db * usr::kGridMeanBlocks);
         ENSURE(c->d_W, db * 9);
@@ -555,8 +564,24 @@ usr_status check_device(const usr_ctx* c)
 void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
 {
     usr::launch_bin_cells(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
-                          c->d_cell_start, c->d_pstart, c->d_unsorted, c->d_perm, c->d_spos, c->d_cpos, c->d_cidx,
-                          c->d_ccell, c->d_bblo, c->d_bbhi, c->d_status, st);
+                          c->d_cell_start, c->d_pstart, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_unsorted, c->d_perm,
+                          c->d_spos, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_nacc, c->d_status,
+                          st);
+}
+
+usr::ClusterList cluster_list(const usr_ctx* c)
+{
+    usr::ClusterList L;
+    L.cpos = c->d_cpos;
+    L.cidx = c->d_cidx;
+    L.ccell = c->d_ccell;
+    L.bblo = c->d_bblo;
+    L.bbhi = c->d_bbhi;
+    L.pstart = c->d_pstart;
+    L.gfull = c->d_gfull;
+    L.gpart = c->d_gpart;
+    L.gfirst = c->d_gfirst;
+    return L;
 }
 
 /* The evaluation sequence; xyzq/out are device pointers already checked. */
@@ -657,13 +682,13 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
     mark(8, sd);
     if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
-    usr::launch_near(c->max_clusters, P.poly_deg, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi,
-                     c->d_pstart, c->near, c->d_near, st, c->vir ? c->d_vnear : nullptr);
+    usr::launch_near(c->max_groups, P.poly_deg, cluster_list(c), c->near, c->d_queue, c->d_nacc,
+                     c->vir ? c->d_vnear : nullptr, c->d_status, st);
     mark(2, st);
     // join
     if (cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return USR_ERR_CUDA;
     mark(9, st);
-    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_near, c->d_psi, c->grid, out,
+    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_nacc, c->d_psi, c->grid, out,
                        c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
                        c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
     mark(10, st);
@@ -674,7 +699,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
             fp32_conv(c, rho, c->d_vtab[cmp], c->d_psiv, st, [](int) {});
             usr::launch_grid_dot(c->grid, rho, c->d_psiv, 0.5, c->d_vpart, c->d_counters + 3, c->d_vdot + cmp, st);
         }
-        usr::launch_virial_finalize(c->d_vnear, usr::near_warps(c->max_clusters), c->d_vdot, en, c->d_W, st);
+        usr::launch_virial_finalize(c->d_vnear, cluster_list(c), c->ncell, c->d_vdot, en, c->d_W, st);
     }
     usr_status s = check_launch();
     if (s == USR_OK) {
@@ -829,7 +854,7 @@ extern "C" usr_status usr_last_device_status(usr_ctx* c)
     int v = 0;
     if (cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return USR_ERR_CUDA;
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return USR_ERR_CUDA;
-    if (v & 1) return USR_ERR_NONFINITE;
+    if (v & 9) return USR_ERR_NONFINITE;
     if (v & 4) return USR_ERR_TIMEOUT;
     return (v & 2) ? USR_ERR_INTERNAL : USR_OK;
 }
@@ -861,8 +886,7 @@ extern "C" usr_status usr_debug_pairs(usr_ctx* c, int n, const float* xyzq, int*
     if (n == 0) return USR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     bin_and_cluster(c, n, (const float4*)xyzq, st);
-    usr::launch_pairs(c->max_clusters, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_pstart, c->d_perm,
-                      c->near, count, (unsigned long long*)hash, st);
+    usr::launch_pairs(c->max_clusters, cluster_list(c), c->d_perm, c->near, count, (unsigned long long*)hash, st);
     return check_launch();
 }
 

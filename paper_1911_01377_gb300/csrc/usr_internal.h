@@ -109,6 +109,25 @@ struct NearArgs {
     float poly[kMaxPolyDeg + 1];
 };
 
+/*
+ * The cell list as the pair kernels read it: 8-slot clusters (paired layout,
+ * see k_cell_build) with their caller-sorted indices (-1 for padding rows),
+ * cells, bounding boxes, per-cell padded slot starts, and the groups of
+ * consecutive clusters of one cell that one warp of the half-list kernel owns
+ * (per-cell group starts, first cluster of each group).
+ */
+struct ClusterList {
+    const float4* cpos;
+    const int* cidx;
+    const int* ccell;
+    const float4* bblo;
+    const float4* bbhi;
+    const int* pstart;
+    const int* gfull;     // per cell: first full group (scan), total at [ncell]
+    const int* gpart;     // per cell: its partial group's index after the full ones (scan), total at [ncell]
+    const int* gfirst;
+};
+
 struct GridArgs {
     BoxF box;
     float hh[3];          // h^2 / (2 sigma_s^2): exponent factor per stencil step
@@ -172,22 +191,26 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
                        float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
                        int* status, cudaStream_t st);
 void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                      float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
-                      float4* cpos, int* cidx, int* ccell, float4* bblo, float4* bbhi, int* status, cudaStream_t st);
-void launch_near(int max_clusters, int deg, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
-                 const float4* bbhi, const int* pstart, const NearArgs& a, float4* out, cudaStream_t st,
-                 double* vir = nullptr);
-int near_warps(int max_clusters);
-void launch_pairs(int max_clusters, const float4* cpos, const int* cidx, const int* ccell, const float4* bblo,
-                  const float4* bbhi, const int* pstart, const int* perm, const NearArgs& a, int* count,
+                      float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
+                      int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
+                      float4* bbhi, unsigned long long* near_acc, int* status, cudaStream_t st);
+/* Upper bound of the half-list kernel's groups for n atoms in ncell cells; clusters per group. */
+int near_max_groups(int n, int ncell);
+int near_group_clusters();
+/* Work units (virial slots) of the half-list kernel over max_groups groups; neighbour ranges per group. */
+int near_units(int max_groups);
+int near_splits();
+void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& a, int* queue,
+                 unsigned long long* acc, double* vir, int* status, cudaStream_t st);
+void launch_pairs(int max_clusters, const ClusterList& L, const int* perm, const NearArgs& a, int* count,
                   unsigned long long* hash, cudaStream_t st);
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
                    void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
                    cudaStream_t st, float* rho32 = nullptr);
 void launch_grid_dot(const GridArgs& g, const float* a, const float* b, double scale, double* partial,
                      unsigned int* counter, double* out, cudaStream_t st);
-void launch_virial_finalize(const double* near_w, int nwarps, const double* dots, const double* energy, double* W,
-                            cudaStream_t st);
+void launch_virial_finalize(const double* near_w, const ClusterList& L, int ncell, const double* dots,
+                            const double* energy, double* W, cudaStream_t st);
 void launch_conv(const ConvGemm& g, int batches, cudaStream_t st);
 void launch_fp32_tables(const ConvTableArgs& t, float* Bx, float* Ay, float* Az, float* wx, float* wy, float* wz,
                         cudaStream_t st);
@@ -199,7 +222,8 @@ usr_status conv_tc_setup(bool bf16, size_t smem);
 void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int batches, cudaStream_t st);
 void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
                       cudaStream_t st);
-void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const float4* near_out,
+void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm,
+                   const unsigned long long* near_acc,
                    const float* psi, const GridArgs& g, float4* out, float4* near_dbg,
                    float4* far_dbg, double* partial, unsigned int* counter, double* energy, int* status,
                    cudaStream_t st);

@@ -94,12 +94,13 @@ def lib():
         L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
         L.usr_stage_times.argtypes = [_c_p, ctypes.POINTER(ctypes.c_float)]
+        L.usr_fp32_peak.argtypes = [ctypes.POINTER(_c_d)]
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
                      "usr_eval_host",
                      "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
                      "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_server_create", "usr_server_submit",
                      "usr_server_wait", "usr_server_info",
-                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times"):
+                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times", "usr_fp32_peak"):
             getattr(L, name).restype = _c_i
         _lib = L
     return _lib
@@ -215,6 +216,13 @@ def usr_set_keep_parts(ctx, on: bool):
 
 def usr_debug_parts(ctx, near_ptr, far_ptr, stream=None):
     _check(lib().usr_debug_parts(ctx, near_ptr, far_ptr, _stream_ptr(stream)), "usr_debug_parts")
+
+
+def usr_fp32_peak() -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s)."""
+    v = _c_d(0.0)
+    _check(lib().usr_fp32_peak(ctypes.byref(v)), "usr_fp32_peak")
+    return float(v.value)
 
 
 def usr_set_profiling(ctx, on: bool):
