@@ -334,6 +334,20 @@ usr_status usr_virial(usr_ctx* ctx, double* W, void* stream);
 usr_status usr_set_keep_parts(usr_ctx* ctx, int on);
 
 /*
+ * Test hook of the failure path (the paper has no counterpart).  With on = 1,
+ * the next usr_eval of a tensor-core context (TF32X3 or BF16X3) makes its
+ * first convolution pass wait on a barrier that nothing completes; the wait is
+ * bounded at 1 ms, as every wait of those kernels is bounded, and runs out.
+ * Each CTA of the pass then takes the kernel's own abort path: it raises the
+ * timeout bit, waits for its copies in flight, frees its tensor memory and
+ * returns, so the context stays usable.  That evaluation's results are not
+ * valid and usr_last_device_status reports USR_ERR_TIMEOUT; the hook then
+ * clears itself, and the next evaluation is a normal one.  USR_ERR_ARG for an
+ * FP32 context.  No GPU fault, trap or unbounded wait is involved.
+ */
+usr_status usr_debug_inject_timeout(usr_ctx* ctx, int on);
+
+/*
  * Near and far parts of the last usr_eval on this context (which must have
  * run with usr_set_keep_parts on; USR_ERR_ARG otherwise), caller order, n
  * rows float4 each (device; either may be NULL):

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
     int cy = canon_cell(yw, b.cs[1], b.nc[1]);
     int cz = canon_cell(zw, b.cs[2], b.nc[2]);
     int c = (cz * b.nc[1] + cy) * b.nc[0] + cx;
+    if (!USR_IN_BOUNDS(c, b.nc[0] * b.nc[1] * b.nc[2], status)) c = 0;
     cell_of[i] = c;
     slot[i] = atomicAdd(&count[c], 1);
     wpos[i] = make_float4(xw, yw, zw, (ok && isfinite(p.w)) ? p.w : 0.0f);
@@ -132,11 +133,13 @@ __global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict_
 }
 
 __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
-                                               const int* __restrict__ start, int* __restrict__ unsorted)
+                                               const int* __restrict__ start, int* __restrict__ unsorted,
+                                               int* __restrict__ status)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    unsorted[start[cell_of[i]] + slot[i]] = i;
+    const int d = start[cell_of[i]] + slot[i];
+    if (USR_IN_BOUNDS(d, n, status)) unsorted[d] = i;
 }
 
 /*
@@ -148,10 +151,10 @@ __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ ce
 constexpr int kSortThreads = 128;
 constexpr int kSortMax = 2048;
 
-__global__ void __launch_bounds__(kSortThreads) k_cell_sort(const int* __restrict__ start,
+__global__ void __launch_bounds__(kSortThreads) k_cell_sort(int n, const int* __restrict__ start,
                                                             const int* __restrict__ unsorted,
                                                             const float4* __restrict__ wpos, int* __restrict__ perm,
-                                                            float4* __restrict__ spos)
+                                                            float4* __restrict__ spos, int* __restrict__ status)
 {
     __shared__ int v[kSortMax];
     const int c = blockIdx.x;
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(const int* __restric
         const int x = src[e];
         int r = 0;
         for (int f = 0; f < m; ++f) r += src[f] < x;
+        if (!USR_IN_BOUNDS(s0 + r, n, status) || !USR_IN_BOUNDS(x, n, status)) continue;
         perm[s0 + r] = x;
         spos[s0 + r] = wpos[x];
     }
@@ -231,7 +235,8 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
                                                              int* __restrict__ cidx, int* __restrict__ ccell,
                                                              float4* __restrict__ bblo, float4* __restrict__ bbhi,
                                                              int* __restrict__ gfirst,
-                                                             unsigned long long* __restrict__ acc)
+                                                             unsigned long long* __restrict__ acc, int n,
+                                                             int max_slots, int max_groups, int* __restrict__ status)
 {
     __shared__ int v[kSortMax];
     __shared__ int ks[kSortMax];
@@ -248,10 +253,16 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
         // full groups in cell order, then the partial ones (the pair kernel takes them in that order,
         // so its last work units are the small ones)
         const int f0 = gfull[c], nf = gfull[c + 1] - f0;
-        for (int k = threadIdx.x; k < nf; k += kSortThreads) gfirst[f0 + k] = (p0 >> 3) + k * gcl;
-        if (threadIdx.x == 0 && gpart[c + 1] > gpart[c]) gfirst[gfull[b.nc[0] * b.nc[1] * b.nc[2]] + gpart[c]] = (p0 >> 3) + nf * gcl;
-        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc + 4 * (size_t)s0);
-        for (int e = threadIdx.x; e < 2 * m; e += kSortThreads) a2[e] = make_ulonglong2(0ull, 0ull);
+        for (int k = threadIdx.x; k < nf; k += kSortThreads)
+            if (USR_IN_BOUNDS(f0 + k, max_groups, status)) gfirst[f0 + k] = (p0 >> 3) + k * gcl;
+        if (threadIdx.x == 0 && gpart[c + 1] > gpart[c]) {
+            const int gp = gfull[b.nc[0] * b.nc[1] * b.nc[2]] + gpart[c];
+            if (USR_IN_BOUNDS(gp, max_groups, status)) gfirst[gp] = (p0 >> 3) + nf * gcl;
+        }
+        if (USR_IN_BOUNDS(s0 + m - 1, n, status)) {
+            ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc + 4 * (size_t)s0);
+            for (int e = threadIdx.x; e < 2 * m; e += kSortThreads) a2[e] = make_ulonglong2(0ull, 0ull);
+        }
     }
     if (in_smem)
         for (int e = threadIdx.x; e < m; e += kSortThreads) v[e] = unsorted[s0 + e];
@@ -262,6 +273,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
         const int x = src[e];
         int r = 0;
         for (int f = 0; f < m; ++f) r += src[f] < x;
+        if (!USR_IN_BOUNDS(s0 + r, n, status) || !USR_IN_BOUNDS(x, n, status)) continue;
         const float4 p = wpos[x];
         perm[s0 + r] = x;
         spos[s0 + r] = p;
@@ -275,10 +287,12 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
             const int kf = kk[f];
             r += (kf < ke) || (kf == ke && f < e);
         }
+        if (!USR_IN_BOUNDS(p0 + r, max_slots, status)) continue;
         pk_store(cp, p0 + r, spos[s0 + e]);
         cidx[p0 + r] = s0 + e;
     }
     for (int e = m + threadIdx.x; e < pm; e += kSortThreads) {
+        if (!USR_IN_BOUNDS(p0 + e, max_slots, status)) continue;
         // padding rows: far from the box, so never within r_c of an atom, and 4e4 A apart within
         // a cluster (rows of different cells may coincide; the pair kernel never uses their sums)
         const float far = -1.0e6f - 4.0e4f * (float)(e & 7);
@@ -297,6 +311,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
             hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
         }
         const int cl = (p0 >> 3) + k;
+        if (!USR_IN_BOUNDS(cl, max_slots >> 3, status)) continue;
         bblo[cl] = lo;
         bbhi[cl] = hi;
         ccell[cl] = c;
@@ -314,9 +329,9 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, nullptr, nullptr, 1, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
+    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cell_sort<<<ncell, kSortThreads, 0, st>>>(cell_start, unsorted, wpos, perm, spos);
+    k_cell_sort<<<ncell, kSortThreads, 0, st>>>(n, cell_start, unsorted, wpos, perm, spos, status);
     return cudaGetLastError();
 }
 
@@ -324,17 +339,19 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
 void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                       float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
                       int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
-                      float4* bbhi, unsigned long long* near_acc, int* status, cudaStream_t st)
+                      float4* bbhi, unsigned long long* near_acc, int max_clusters, int max_groups, int* status,
+                      cudaStream_t st)
 {
     const int gcl = near_group_clusters();
     cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
     int nb = (n + 255) / 256;
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, gfull, gpart, gcl, queue);
-    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted);
+    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted, status);
     // slot[] is free after placement: it holds the Morton keys of cells too large for shared memory
     k_cell_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, gfull, gpart, gcl, unsorted, wpos, b, perm, spos,
-                                                  slot, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc);
+                                                  slot, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc, n,
+                                                  8 * max_clusters, max_groups, status);
 }
 
 }  // namespace usr

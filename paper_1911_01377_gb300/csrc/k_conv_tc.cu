@@ -35,6 +35,9 @@
  * lanes 32w..32w+31, one line per thread).  Every wait is bounded in time:
  * on expiry the CTA raises the timeout bit of the status word, waits (again
  * bounded) for its copies in flight, frees its tensor memory and returns.
+ * For tests, inject_wait_ns != 0 makes the MMA issuer first wait on a barrier
+ * that no thread ever arrives at, bounded by that limit, so that this path
+ * runs without any fault.
  */
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -83,15 +86,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 }
 
 /*
- * Bounded wait for the phase of `parity`: false on timeout, or (when
+ * Bounded wait for the phase of `parity`: false after limit_ns, or (when
  * abort_flag is given) as soon as another role of the CTA has aborted.
  */
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag)
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                          unsigned long long limit_ns = kWaitNs)
 {
     const unsigned long long t0 = globaltimer();
     while (!mbar_try(bar, parity)) {
         if (abort_flag && *abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
 }
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     constexpr int KSTAGE = BF16 ? 64 : 32;             // K per 128-byte row
     constexpr int KSUB = KSTAGE / KMMA;                // MMAs per stage and operand pair (4)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bars[2 * kConvTcMaxStages + 1];
+    __shared__ __align__(8) unsigned long long bars[2 * kConvTcMaxStages + 2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_flag;
 
@@ -203,6 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kConvTcMaxStages]);
     const uint32_t done = smem_u32(&bars[2 * kConvTcMaxStages]);
+    const uint32_t never = smem_u32(&bars[2 * kConvTcMaxStages + 1]);   // no thread ever arrives here
     const int nk = (g.K + KSTAGE - 1) / KSTAGE;
 
     if (threadIdx.x == 0) {
@@ -212,6 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(done, 1);
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -252,6 +258,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                          | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10)   // A, B: BF16 or TF32
                          | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         bool ok = true;
+        if (g.inject_wait_ns && !mbar_wait(never, 0, &abort_flag, g.inject_wait_ns)) {
+            // the test form of a wait that runs out: same abort path as a real one
+            atomicOr(g.status, 4);
+            abort_flag = 1;
+            ok = false;
+        }
         for (int kb = 0; kb < nk && ok; ++kb) {
             const int s = kb % S, use = kb / S;
             if (!mbar_wait(full0 + 8 * s, use & 1, &abort_flag)) {
@@ -318,13 +330,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                 if (c >= g.cols || m >= g.n_out) continue;
                 if (g.pass == 1) {
                     const float val = fmaf(muj, dc, v[i]);
-                    store_split<BF16>(g.out_hi, g.out_lo, (size_t)(batch * g.nx + m) * g.lines + line, val);
+                    const size_t idx = (size_t)(batch * g.nx + m) * g.lines + line;
+                    if (USR_IN_BOUNDS(idx, g.out_elems, g.status)) store_split<BF16>(g.out_hi, g.out_lo, idx, val);
                 } else if (g.pass == 2) {
                     const float val = fmaf(muj, dc, v[i]);
                     const size_t idx = ((size_t)(m * g.nx + lx) * g.nterms + batch) * g.nz + lz;
-                    store_split<BF16>(g.out_hi, g.out_lo, idx, val);
+                    if (USR_IN_BOUNDS(idx, g.out_elems, g.status)) store_split<BF16>(g.out_hi, g.out_lo, idx, val);
                 } else {
-                    static_cast<float*>(g.out_hi)[(size_t)m * g.lines + line] = v[i] + dc;
+                    const size_t idx = (size_t)m * g.lines + line;
+                    if (USR_IN_BOUNDS(idx, g.out_elems, g.status)) static_cast<float*>(g.out_hi)[idx] = v[i] + dc;
                 }
             }
         }

@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
         const int nch = min(kChunk, natoms - c0);
         // phase 1: stage the chunk's positions, then per-atom 1D weights (q folded
         // into the x weights) and tile base
-        for (int a = threadIdx.x; a < nch; a += kThreads) sp[a] = pos[block_atom(c0 + a, rs, pre)];
+        for (int a = threadIdx.x; a < nch; a += kThreads) {
+            const int s = block_atom(c0 + a, rs, pre);
+            sp[a] = USR_IN_BOUNDS(s, g.max_atoms, status) ? pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         __syncthreads();
         for (int idx = threadIdx.x; idx < nch * 3 * P; idx += kThreads) {
             const int a = idx / (3 * P), rem = idx - a * 3 * P;
@@ -297,7 +300,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
 template <int SPLIT>
 __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __restrict__ tilebuf,
                                                      const double* __restrict__ mean, void* __restrict__ rho,
-                                                     void* __restrict__ rho_lo, float* __restrict__ rho32)
+                                                     void* __restrict__ rho_lo, float* __restrict__ rho32,
+                                                     int* __restrict__ status)
 {
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
     const long long G = (long long)n0 * n1 * n2;
@@ -319,7 +323,8 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
             const long long rowbase = ((long long)(bz.x * nb1 + by.x) * nb0) * TT + ((long long)bz.y * T1 + by.y) * T0;
             for (int ix = 0; ix < cx; ++ix) {
                 const int2 bx = px[ix];
-                s += __ldg(tilebuf + rowbase + (long long)bx.x * TT + bx.y);
+                const long long t = rowbase + (long long)bx.x * TT + bx.y;
+                if (USR_IN_BOUNDS(t, (long long)nb0 * nb1 * g.tg.nbk[2] * TT, status)) s += __ldg(tilebuf + t);
             }
         }
     }
@@ -493,10 +498,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict
         const int nch = min(kGChunk, natoms - c0);
         __syncthreads();                           // the previous chunk is done
         for (int a = threadIdx.x; a < nch; a += kThreads) {
-            const int s = block_atom(c0 + a, rs, pre);
+            int s = block_atom(c0 + a, rs, pre);
+            if (!USR_IN_BOUNDS(s, g.max_atoms, status)) s = 0;
             sp[a] = pos[s];
             sn[a] = near_part(near_acc, s);
-            si[a] = perm[s];
+            const int ci = perm[s];
+            si[a] = USR_IN_BOUNDS(ci, g.max_atoms, status) ? ci : -1;
         }
         __syncthreads();
         for (int j0 = warp * 8; j0 < nch; j0 += kWarps * 8) {
@@ -575,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict
                 az += __shfl_xor_sync(0xffffffffu, az, o);
             }
             aphi -= phi_dc;
-            if (have && u == 0) {
+            if (have && u == 0 && si[j] >= 0) {
                 const int i = si[j];
                 const float qi = p.w;
                 const float4 nr = sn[j];
@@ -684,11 +691,11 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
     const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
     const unsigned nr = (unsigned)((G + 255) / 256);
     if (split == 1)
-        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32);
+        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32, status);
     else if (split == 2)
-        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32);
+        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32, status);
     else
-        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr);
+        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr, status);
 }
 
 #define USR_GATHER_CASE(PP)                                                                                      \

@@ -204,9 +204,12 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
 {
     const int lane = threadIdx.x & 31;
     const int ncx = a.box.nc[0], ncy = a.box.nc[1], ncz = a.box.nc[2];
+    if (!USR_IN_BOUNDS(grp, a.max_groups, status)) return;
     const int c0 = L.gfirst[grp];
+    if (!USR_IN_BOUNDS(c0, a.max_clusters, status)) return;
     const int cell = L.ccell[c0];
     const int ni = min(GI, (L.pstart[cell + 1] >> 3) - c0);
+    if (!USR_IN_BOUNDS(c0 + ni - 1, a.max_clusters, status)) return;
     const int jl = lane & 7, gi = lane >> 3;
     NearI I[GI];
     #pragma unroll
@@ -253,7 +256,7 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
         for (int jb = jc0; jb < jc1; jb += 32) {
             const int jc = jb + lane;
             unsigned int m = 0;
-            if (jc < jc1) {
+            if (jc < jc1 && USR_IN_BOUNDS(jc, a.max_clusters, status)) {
                 const float4 lo = L.bblo[jc], hi = L.bbhi[jc];
                 const float lx = __fadd_rn(lo.x, sx), ly = __fadd_rn(lo.y, sy), lz = __fadd_rn(lo.z, sz);
                 const float hx = __fadd_rn(hi.x, sx), hy = __fadd_rn(hi.y, sy), hz = __fadd_rn(hi.z, sz);
@@ -308,7 +311,8 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
                 const float k0 = (b1 ? vz : vx) + r0, k1 = (b1 ? vp : vy) + r1;
                 const float r2 = __shfl_xor_sync(0xffffffffu, b0 ? k0 : k1, 8);
                 const float v = (b0 ? k1 : k0) + r2;                           // component gi of atom jl
-                if (sj >= 0) red_fix(acc + 4 * (size_t)sj + gi, gi < 3 ? -qj * v : v, status);
+                if (sj >= 0 && USR_IN_BOUNDS(sj, a.max_atoms, status))
+                    red_fix(acc + 4 * (size_t)sj + gi, gi < 3 ? -qj * v : v, status);
             }
         }
     }
@@ -338,7 +342,8 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
         const int slot = (c0 + k) * 8 + gi + 4 * (jl >> 2);
         const int si = L.cidx[slot];
         const float qi = c2 ? I[k].q.y : I[k].q.x;
-        if (si >= 0) red_fix(acc + 4 * (size_t)si + comp, comp < 3 ? qi * v : v, status);
+        if (si >= 0 && USR_IN_BOUNDS(si, a.max_atoms, status))
+            red_fix(acc + 4 * (size_t)si + comp, comp < 3 ? qi * v : v, status);
     }
     if (VIR) {
         const f2 vv[6] = {V.xx, V.yy, V.zz, V.xy, V.xz, V.yz};
@@ -391,13 +396,14 @@ __global__ void __launch_bounds__(128, GI >= 4 ? 4 : 5) k_near_half(ClusterList 
  * count and the sum of splitmix64 of the partners' caller indices.
  */
 __global__ void __launch_bounds__(128) k_pairs_count(ClusterList L, const int* __restrict__ perm, NearArgs a,
-                                                     int* __restrict__ count, unsigned long long* __restrict__ hash)
+                                                     int* __restrict__ count, unsigned long long* __restrict__ hash,
+                                                     int* __restrict__ status)
 {
     const int ncx = a.box.nc[0], ncy = a.box.nc[1], ncz = a.box.nc[2];
     const int ncl = L.pstart[ncx * ncy * ncz] >> 3;
     const int ic = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (ic >= ncl) return;
+    if (ic >= ncl || !USR_IN_BOUNDS(ic, a.max_clusters, status)) return;
     const int il = lane >> 2, g = lane & 3;
     const int islot = ic * 8 + il;
     const float* cf = reinterpret_cast<const float*>(L.cpos);
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(128) k_pairs_count(ClusterList L, const int* _
         for (int jb = jc0; jb < jc1; jb += 32) {
             const int jc = jb + lane;
             bool near = false;
-            if (jc < jc1) {
+            if (jc < jc1 && USR_IN_BOUNDS(jc, a.max_clusters, status)) {
                 const float4 lo = L.bblo[jc], hi = L.bbhi[jc];
                 const float gx = fmaxf(0.f, fmaxf(__fsub_rn(__fadd_rn(lo.x, sx), bhi.x), __fsub_rn(blo.x, __fadd_rn(hi.x, sx))));
                 const float gy = fmaxf(0.f, fmaxf(__fsub_rn(__fadd_rn(lo.y, sy), bhi.y), __fsub_rn(blo.y, __fadd_rn(hi.y, sy))));
@@ -460,8 +466,10 @@ __global__ void __launch_bounds__(128) k_pairs_count(ClusterList L, const int* _
     const int si = L.cidx[islot];
     if (g == 0 && si >= 0) {
         const int ci = perm[si];
-        count[ci] = cnt;
-        hash[ci] = h;
+        if (USR_IN_BOUNDS(ci, a.max_atoms, status)) {
+            count[ci] = cnt;
+            hash[ci] = h;
+        }
     }
 }
 
@@ -547,10 +555,10 @@ void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& 
 }
 
 void launch_pairs(int max_clusters, const ClusterList& L, const int* perm, const NearArgs& a, int* count,
-                  unsigned long long* hash, cudaStream_t st)
+                  unsigned long long* hash, int* status, cudaStream_t st)
 {
     const int blocks = (max_clusters + 3) / 4;
-    k_pairs_count<<<blocks, 128, 0, st>>>(L, perm, a, count, hash);
+    k_pairs_count<<<blocks, 128, 0, st>>>(L, perm, a, count, hash, status);
 }
 
 }  // namespace usr

@@ -15,6 +15,7 @@
 #include <unordered_map>
 
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "usr_internal.h"
 
@@ -22,6 +23,14 @@ using usr::Plan;
 
 // profiling events of one evaluation (stage boundaries on the two streams)
 constexpr int kProfEvents = 11;
+
+/* Host-side NVTX range around the enqueueing of one stage (no cost unless a tool is attached). */
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct usr_ctx {
     Plan plan;
@@ -78,6 +87,7 @@ struct usr_ctx {
     // host-buffer staging and inspection
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
     bool keep_parts = false;
+    bool inject_timeout = false;   // the next evaluation's first tensor-core pass waits on a barrier nothing completes
     bool parts_valid = false;
     // the far chain (spread, convolutions, psi mean) runs on `side`, a high-priority stream forked from and
     // joined back to the caller's stream, while the pair kernel runs on the caller's stream
@@ -465,6 +475,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
             a.out_hi = o_hi[ps];
             a.out_lo = o_lo[ps];
             a.status = c->d_status;
+            a.out_elems = ps == 2 ? (long long)G : (long long)G * (long long)N;
             c->tbatches[ps] = batches[ps];
             const long long b_rows = (long long)batches[ps] * a.ntiles * a.NT;
             if ((s = usr::make_tmap(&c->maps[ps].a_hi, a_hi[ps], bf, a_rows[ps], a.K, 128)) ||
@@ -530,6 +541,9 @@ void fill_args(usr_ctx* c)
     usr::NearArgs& a = c->near;
     std::memset(&a, 0, sizeof(a));
     a.box = c->boxf;
+    a.max_atoms = c->max_atoms > 0 ? c->max_atoms : 1;
+    a.max_clusters = c->max_clusters;
+    a.max_groups = c->max_groups;
     a.rc2 = (float)(P.p.r_c * P.p.r_c);
     a.two_over_rc2 = (float)(2.0 / (P.p.r_c * P.p.r_c));
     a.n_explicit = P.n_explicit;
@@ -543,6 +557,7 @@ void fill_args(usr_ctx* c)
     usr::GridArgs& g = c->grid;
     std::memset(&g, 0, sizeof(g));
     g.box = c->boxf;
+    g.max_atoms = c->max_atoms > 0 ? c->max_atoms : 1;
     for (int ax = 0; ax < 3; ++ax) {
         g.hh[ax] = (float)(P.h[ax] * P.h[ax] / (2.0 * P.sigma_sa[ax] * P.sigma_sa[ax]));
         g.dfac[ax] = (float)(P.h[ax] / (P.sigma_sa[ax] * P.sigma_sa[ax]));
@@ -565,8 +580,8 @@ void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
 {
     usr::launch_bin_cells(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
                           c->d_cell_start, c->d_pstart, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_unsorted, c->d_perm,
-                          c->d_spos, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_nacc, c->d_status,
-                          st);
+                          c->d_spos, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_nacc,
+                          c->max_clusters, c->max_groups, c->d_status, st);
 }
 
 usr::ClusterList cluster_list(const usr_ctx* c)
@@ -653,46 +668,63 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     auto mark = [&](int k, cudaStream_t s) {
         if (c->prof) cudaEventRecord(c->ev[k], s);
     };
+    NvtxRange r_eval("usr_eval");
     mark(0, st);
-    bin_and_cluster(c, n, xyzq, st);
+    {
+        NvtxRange r("usr: cell list");
+        bin_and_cluster(c, n, xyzq, st);
+    }
     mark(1, st);
     // fork: the far chain on the side stream (first, so that its few large CTAs are placed before the
     // pair kernel's many small ones fill the SMs), the pair kernel on the caller's stream
     if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev_fork, 0) != cudaSuccess)
         return USR_ERR_CUDA;
     cudaStream_t sd = c->side;
-    mark(3, sd);
-    if (c->tc)
-        usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
-                           c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd,
-                           c->vir ? c->d_rho32 : nullptr);
-    else
-        usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
-                           c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd);
-    mark(4, sd);
-    if (c->tc) {
-        for (int p = 0; p < 3; ++p) {
-            usr::launch_conv_tc(c->tc_bf16, c->maps[p], c->targs[p], c->tbatches[p], sd);
-            mark(5 + p, sd);
+    {
+        NvtxRange r("usr: far chain (spread, convolutions, psi mean)");
+        mark(3, sd);
+        if (c->tc)
+            usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
+                               c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status,
+                               sd, c->vir ? c->d_rho32 : nullptr);
+        else
+            usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
+                               c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd);
+        mark(4, sd);
+        if (c->tc) {
+            for (int p = 0; p < 3; ++p) {
+                usr::ConvTcArgs ta = c->targs[p];
+                ta.inject_wait_ns = (p == 0 && c->inject_timeout) ? 1000000ull : 0ull;   // 1 ms, one evaluation
+                usr::launch_conv_tc(c->tc_bf16, c->maps[p], ta, c->tbatches[p], sd);
+                mark(5 + p, sd);
+            }
+            c->inject_timeout = false;
+        } else {
+            float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
+            fp32_conv(c, c->d_rho, t, c->d_psi, sd, [&](int k) { mark(5 + k, sd); });
         }
-    } else {
-        float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
-        fp32_conv(c, c->d_rho, t, c->d_psi, sd, [&](int k) { mark(5 + k, sd); });
+        usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
+        mark(8, sd);
+        if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
     }
-    usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
-    mark(8, sd);
-    if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
-    usr::launch_near(c->max_groups, P.poly_deg, cluster_list(c), c->near, c->d_queue, c->d_nacc,
-                     c->vir ? c->d_vnear : nullptr, c->d_status, st);
-    mark(2, st);
+    {
+        NvtxRange r("usr: near pairs");
+        usr::launch_near(c->max_groups, P.poly_deg, cluster_list(c), c->near, c->d_queue, c->d_nacc,
+                         c->vir ? c->d_vnear : nullptr, c->d_status, st);
+        mark(2, st);
+    }
     // join
     if (cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return USR_ERR_CUDA;
     mark(9, st);
-    usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_nacc, c->d_psi, c->grid, out,
-                       c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
-                       c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
-    mark(10, st);
+    {
+        NvtxRange r("usr: gather + energy");
+        usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_nacc, c->d_psi, c->grid, out,
+                           c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
+                           c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
+        mark(10, st);
+    }
     if (c->vir) {
+        NvtxRange r("usr: virial");
         // far virial: 1/2 <rho, psi_ab> per strain component, then the finalisation with E_far
         const float* rho = c->tc ? c->d_rho32 : c->d_rho;
         for (int cmp = 0; cmp < 6; ++cmp) {
@@ -856,7 +888,7 @@ extern "C" usr_status usr_last_device_status(usr_ctx* c)
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return USR_ERR_CUDA;
     if (v & 9) return USR_ERR_NONFINITE;
     if (v & 4) return USR_ERR_TIMEOUT;
-    return (v & 2) ? USR_ERR_INTERNAL : USR_OK;
+    return (v & 18) ? USR_ERR_INTERNAL : USR_OK;
 }
 
 extern "C" usr_status usr_debug_cells(usr_ctx* c, int n, const float* xyzq, int* cell, int* perm, int* cell_start,
@@ -886,7 +918,8 @@ extern "C" usr_status usr_debug_pairs(usr_ctx* c, int n, const float* xyzq, int*
     if (n == 0) return USR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     bin_and_cluster(c, n, (const float4*)xyzq, st);
-    usr::launch_pairs(c->max_clusters, cluster_list(c), c->d_perm, c->near, count, (unsigned long long*)hash, st);
+    usr::launch_pairs(c->max_clusters, cluster_list(c), c->d_perm, c->near, count, (unsigned long long*)hash,
+                      c->d_status, st);
     return check_launch();
 }
 
@@ -895,6 +928,13 @@ extern "C" usr_status usr_virial(usr_ctx* c, double* W, void* stream)
     if (!c || !W || !c->vir || !c->vir_valid) return USR_ERR_ARG;
     if (cudaMemcpyAsync(W, c->d_W, 9 * sizeof(double), cudaMemcpyDefault, (cudaStream_t)stream) != cudaSuccess)
         return USR_ERR_CUDA;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_debug_inject_timeout(usr_ctx* c, int on)
+{
+    if (!c || !c->tc) return USR_ERR_ARG;
+    c->inject_timeout = on != 0;
     return USR_OK;
 }
 

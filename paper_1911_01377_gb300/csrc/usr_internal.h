@@ -97,8 +97,24 @@ struct BoxF {
     int n[3];
 };
 
+/*
+ * Debug build (USR_DEBUG_BOUNDS defined): the kernels check their computed
+ * indices against the sizes of the buffers they address; an index out of
+ * range sets bit 16 of the status word (USR_ERR_INTERNAL) and the access is
+ * skipped.  In the normal build the checks compile to nothing.
+ */
+#ifdef USR_DEBUG_BOUNDS
+#define USR_IN_BOUNDS(i, n, status) \
+    ((long long)(i) >= 0 && (long long)(i) < (long long)(n) ? true : (atomicOr((status), 16), false))
+#else
+#define USR_IN_BOUNDS(i, n, status) true
+#endif
+
 struct NearArgs {
     BoxF box;
+    int max_atoms;        // rows of the per-atom buffers (bounds of the debug build)
+    int max_clusters;     // clusters the cluster buffers hold
+    int max_groups;       // groups the group table holds
     float rc2;            // (float)(r_c^2)
     float two_over_rc2;   // 2 / r_c^2
     int n_explicit;
@@ -130,6 +146,7 @@ struct ClusterList {
 
 struct GridArgs {
     BoxF box;
+    int max_atoms;        // rows of the per-atom buffers (bounds of the debug build)
     float hh[3];          // h^2 / (2 sigma_s^2): exponent factor per stencil step
     float dfac[3];        // h / sigma_s^2: derivative factor
     float F0;             // self-interaction constant (per-atom potential)
@@ -173,6 +190,8 @@ struct ConvTcArgs {
     void* out_hi;           // pass output (hi part; FP32 psi for pass 3)
     void* out_lo;           // pass output (lo part; unused for pass 3)
     int* status;
+    unsigned long long inject_wait_ns;   // tests: > 0 makes the pass wait that long on a barrier nothing completes
+    long long out_elems;    // elements of the pass output (bounds of the debug build)
 };
 /* Inputs of the device-side table build (k_tables.cu). */
 struct ConvTableArgs {
@@ -193,7 +212,8 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
 void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                       float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
                       int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
-                      float4* bbhi, unsigned long long* near_acc, int* status, cudaStream_t st);
+                      float4* bbhi, unsigned long long* near_acc, int max_clusters, int max_groups, int* status,
+                      cudaStream_t st);
 /* Upper bound of the half-list kernel's groups for n atoms in ncell cells; clusters per group. */
 int near_max_groups(int n, int ncell);
 int near_group_clusters();
@@ -203,7 +223,7 @@ int near_splits();
 void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& a, int* queue,
                  unsigned long long* acc, double* vir, int* status, cudaStream_t st);
 void launch_pairs(int max_clusters, const ClusterList& L, const int* perm, const NearArgs& a, int* count,
-                  unsigned long long* hash, cudaStream_t st);
+                  unsigned long long* hash, int* status, cudaStream_t st);
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
                    void* rho, void* rho_lo, double* partial, unsigned int* counter, double* mean, int* status,
                    cudaStream_t st, float* rho32 = nullptr);

@@ -58,9 +58,11 @@ def lib():
     """Load libusr.so (built in-tree by paper_1911_01377_gb300.build)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libusr.so not found at {LIB_PATH}: run paper_1911_01377_gb300.build.build()")
-        L = ctypes.CDLL(LIB_PATH)
+        # USR_LIBRARY names another build of the same library (the bounds-checking debug build)
+        path = os.environ.get("USR_LIBRARY") or LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"libusr not found at {path}: run paper_1911_01377_gb300.build.build()")
+        L = ctypes.CDLL(path)
         L.usr_series_preset.argtypes = [_c_i, ctypes.POINTER(usr_series)]
         L.usr_plan.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(usr_plan_info)]
         L.usr_init.argtypes = [ctypes.POINTER(usr_params), ctypes.POINTER(_c_p)]
@@ -95,12 +97,13 @@ def lib():
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
         L.usr_stage_times.argtypes = [_c_p, ctypes.POINTER(ctypes.c_float)]
         L.usr_fp32_peak.argtypes = [ctypes.POINTER(_c_d)]
+        L.usr_debug_inject_timeout.argtypes = [_c_p, _c_i]
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
                      "usr_eval_host",
                      "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
                      "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_server_create", "usr_server_submit",
                      "usr_server_wait", "usr_server_info",
-                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times", "usr_fp32_peak"):
+                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times", "usr_fp32_peak", "usr_debug_inject_timeout"):
             getattr(L, name).restype = _c_i
         _lib = L
     return _lib
@@ -216,6 +219,10 @@ def usr_set_keep_parts(ctx, on: bool):
 
 def usr_debug_parts(ctx, near_ptr, far_ptr, stream=None):
     _check(lib().usr_debug_parts(ctx, near_ptr, far_ptr, _stream_ptr(stream)), "usr_debug_parts")
+
+
+def usr_debug_inject_timeout(ctx, on: bool):
+    _check(lib().usr_debug_inject_timeout(ctx, int(bool(on))), "usr_debug_inject_timeout")
 
 
 def usr_fp32_peak() -> float:

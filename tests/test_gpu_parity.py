@@ -156,6 +156,19 @@ def test_membrane_slab_full_size(torch_cuda, r_c):
     assert O.rms_rel(g["out"][:, 3], ref.phi) < TOL_PHI
 
 
+@pytest.mark.parametrize("r_c", [8.0, 13.0])
+def test_benchmark_timed_form_full_size(torch_cuda, r_c):
+    # the form bench.py times, at its launch configuration: BF16x3 tensor-core convolutions, the GSE-style
+    # spreading of Sec. IV.A (8-point stencil, sigma_s = 0.83 h), full slab; the metric's bound is an rms
+    # relative force error <= 1e-4 against the same-parameter oracle, energy within 1e-6
+    w = workload("membrane_slab")
+    ref = oracle_result("membrane_slab", r_c)
+    _, g = gpu_eval(torch_cuda, w, r_c, keep_parts=False, conv=2, spread_points=8, spread_sigma_over_h=0.83)
+    assert abs(g["E"][0] / ref.E - 1.0) < 1e-6
+    assert O.rms_rel(g["out"][:, :3], ref.F) < 1e-4
+    assert O.rms_rel(g["out"][:, 3], ref.phi) < 1e-4
+
+
 def test_wrapping_and_images(torch_cuda):
     # shifting atoms by whole box vectors changes nothing beyond rounding
     torch = torch_cuda

@@ -235,3 +235,37 @@ def test_virial_diagonal_is_strain_derivative(tables):
     # near part alone is the pair sum 1/2 sum d (x) f: its trace equals sum_i r_i . F_i^near
     # only without images; here just check symmetry
     assert np.allclose(wn, wn.T, rtol=0, atol=1e-13 * np.max(np.abs(wn)))
+
+
+def test_virial_off_diagonal_near_is_shear_derivative(tables):
+    # Off-diagonal components of the near virial, pinned by a shear.  The charges
+    # form a cluster of radius 4 A in a 40 A box with r_c = 5.5 A, so no pair
+    # inside r_c crosses the periodic boundary and E_near is a plain pair sum of
+    # Eq. 20.  Shearing the positions alone (x_a += eps x_b, box unchanged) gives
+    # dE_near/d eps = -sum_i F_i,a x_i,b = -W_near,ab, the pair-virial component
+    # a, b (the centre of the cluster drops out because the near forces sum to
+    # zero).  A swapped or misplaced off-diagonal slot in the oracle's near
+    # virial fails this for some (a, b).
+    rng = np.random.default_rng(23)
+    box = np.array([40.0, 40.0, 40.0])
+    centre = box / 2
+    pts = []
+    while len(pts) < 30:
+        p = centre + rng.uniform(-4.0, 4.0, 3)
+        if np.linalg.norm(p - centre) < 4.0 and all(np.linalg.norm(p - o) >= 1.0 for o in pts):
+            pts.append(p)
+    pos = np.array(pts)
+    q = rng.normal(0.0, 0.6, len(pts))
+    q -= q.mean()
+    ser = _ser(tables, "table2_C1")
+    r_c = 5.5
+    wn, _ = O.virial(ser, r_c, box, pos, q)
+    assert np.max(np.abs(wn - np.diag(np.diag(wn)))) > 1e-3   # the off-diagonal part is not trivially zero
+    h = 1e-6
+    for a, b in [(0, 1), (1, 0), (0, 2), (2, 0), (1, 2), (2, 1)]:
+        def e_near(eps):
+            p = pos.copy()
+            p[:, a] += eps * (pos[:, b] - centre[b])
+            return O.evaluate(ser, r_c, tuple(box), p, q).E_near
+        fd = -(e_near(h) - e_near(-h)) / (2 * h)
+        assert abs(fd - wn[a, b]) < 1e-7 * max(1.0, np.max(np.abs(wn))), (a, b, fd, wn[a, b])
