@@ -329,17 +329,23 @@ def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_fra
     wall_p, lat, bad = serve(arrivals)
     if bad:
         raise RuntimeError(f"serving failures: {bad[:3]}")
-    # one at a time, plain FP32 (one context reconfigured per system, synchronous host-buffer calls)
-    c = usr.USeries(systems[0][0], systems[0][1], systems[0][2], "C1_B2", max_atoms=xs[0].shape[0])
-    big = int(np.argmax([x.shape[0] for x in xs]))
-    c.reconfigure(systems[big][0], systems[big][1], systems[big][2], "C1_B2", max_atoms=xs[big].shape[0])
-    c.eval_host(xs[big], outs[big], ens[big])
-    t0 = time.perf_counter()
-    for (b, g, rc, _), x, o, e in zip(systems, xs, outs, ens):
-        c.reconfigure(b, g, rc, "C1_B2", max_atoms=x.shape[0])
-        c.eval_host(x, o, e)
-    t_one = time.perf_counter() - t0
-    c.close()
+    # one at a time (one context reconfigured per system, synchronous host-buffer calls), in the plain FP32
+    # form and in the served form itself, so that the gain of batching alone is visible
+    def one_at_a_time(**kw):
+        big = int(np.argmax([x.shape[0] for x in xs]))
+        c = usr.USeries(systems[big][0], systems[big][1], systems[big][2], "C1_B2", max_atoms=xs[big].shape[0],
+                        **kw)
+        c.eval_host(xs[big], outs[big], ens[big])
+        t0 = time.perf_counter()
+        for (b, g, rc, _), x, o, e in zip(systems, xs, outs, ens):
+            c.reconfigure(b, g, rc, "C1_B2", max_atoms=x.shape[0], **kw)
+            c.eval_host(x, o, e)
+        t = time.perf_counter() - t0
+        c.close()
+        return t
+
+    t_one = one_at_a_time()
+    t_same = one_at_a_time(conv=conv, spread_points=P, spread_sigma_over_h=ratio)
     return {"systems": len(systems), "charges": n_atoms, "slots": slots, "hbm_budget_gib": budget_gib,
             "form": CHOSEN[0],
             "capacity_atom_evals_per_s": capacity, "all_at_once_wall_s": wall,
@@ -347,7 +353,9 @@ def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_fra
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "throughput_atom_evals_per_s": n_atoms / wall_p,
             "one_at_a_time_fp32_atom_evals_per_s": n_atoms / t_one,
+            "one_at_a_time_same_form_atom_evals_per_s": n_atoms / t_same,
             "speedup_vs_one_at_a_time_fp32": (n_atoms / wall) / (n_atoms / t_one),
+            "speedup_vs_one_at_a_time_same_form": (n_atoms / wall) / (n_atoms / t_same),
             "latency": "submit to results in pinned host memory, host clock"}
 
 

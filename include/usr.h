@@ -212,12 +212,14 @@ usr_status usr_last_device_status(usr_ctx* ctx);
 /*
  * A server evaluates a stream of independent systems (each its own box, grid,
  * cutoff and charges) on the current device.  Requests are queued by
- * usr_server_submit from any host thread; a worker thread admits them in
- * arrival order onto `slots` concurrent evaluation slots, each a context with
- * its own CUDA stream, as soon as a slot is free and the device memory all
- * slots hold stays within hbm_budget_bytes.  Requests that arrive while
- * others run are admitted as slots and memory free up, and their work
- * overlaps on the device.  A slot's context is re-targeted to each request
+ * usr_server_submit from any host thread; `slots` concurrent evaluation
+ * slots, each a context with its own CUDA stream and its own host thread,
+ * take them in arrival order as soon as a slot is free, and admit each once
+ * the device memory all slots hold stays within hbm_budget_bytes.  The host
+ * work of a request (its FP64 plan, table uploads, launches) runs on its
+ * slot's thread, in parallel with the other slots; requests that arrive while
+ * others run are admitted as slots and memory free up, and their device work
+ * overlaps on the GPU.  A slot's context is re-targeted to each request
  * with usr_reconfigure, so cell lists, grids and tables stay resident and are
  * reused; memory is allocated only when a request is larger than anything
  * its slot held before.  The paper has no counterpart: it describes the

@@ -489,69 +489,78 @@ int near_units(int max_groups) { return kNearSplits * max_groups; }
 int near_splits() { return kNearSplits; }
 
 /*
+ * CTAs per SM the pair kernel's instance can hold, and the SM count (once per instance; thread-safe
+ * static initialisation).
+ */
+template <typename K>
+static int2 persistent_shape(K kernel)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    return make_int2(per_sm > 0 ? per_sm : 1, sms > 0 ? sms : 1);
+}
+
+/*
  * Grid of the persistent pair kernel: the CTAs the SMs hold at once, less USR_NEAR_RESERVE per SM
- * (slots left for the far-part kernels of the second stream), at least one per SM.  Measured on the
+ * (slots left for the far-part kernels of the second stream), or at most ctas_per_sm per SM when that
+ * is given (the serving loop runs several systems at once); at least one per SM.  Measured on the
  * membrane slab, the pair kernel with every slot (reserve 0) gives the shortest evaluation: it runs
  * 13% faster than with one slot per SM left free, and the far chain, latency-bound, gains less from
  * running beside it than the pair kernel loses.
  */
-template <typename K>
-static int persistent_grid(K kernel)
+static int persistent_grid(int2 shape, int ctas_per_sm, int units_max)
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
-    per_sm = per_sm - USR_NEAR_RESERVE;
+    int per_sm = shape.x - USR_NEAR_RESERVE;
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     if (per_sm < 1) per_sm = 1;
-    return per_sm * sms;
+    return std::max(1, std::min(per_sm * shape.y, (units_max + 3) / 4));
 }
 
 template <int GI, int DEG, int NEXP>
 static void launch_half(int max_groups, const ClusterList& L, const NearArgs& a, int* queue, unsigned long long* acc,
-                        double* vir, int* status, cudaStream_t st)
+                        double* vir, int* status, int ctas_per_sm, cudaStream_t st)
 {
     const int units_max = kNearSplits * max_groups;
     if (vir) {
-        static const int grid = persistent_grid(k_near_half<GI, DEG, NEXP, true>);
-        k_near_half<GI, DEG, NEXP, true><<<std::min(grid, (units_max + 3) / 4), 128, 0, st>>>(L, a, queue, acc, vir,
-                                                                                               status);
+        static const int2 shape = persistent_shape(k_near_half<GI, DEG, NEXP, true>);
+        k_near_half<GI, DEG, NEXP, true><<<persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st>>>(
+            L, a, queue, acc, vir, status);
     } else {
-        static const int grid = persistent_grid(k_near_half<GI, DEG, NEXP, false>);
-        k_near_half<GI, DEG, NEXP, false><<<std::min(grid, (units_max + 3) / 4), 128, 0, st>>>(L, a, queue, acc,
-                                                                                                nullptr, status);
+        static const int2 shape = persistent_shape(k_near_half<GI, DEG, NEXP, false>);
+        k_near_half<GI, DEG, NEXP, false><<<persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st>>>(
+            L, a, queue, acc, nullptr, status);
     }
 }
 
 /* One explicit Gaussian (the common case: the narrow j = 0 term) unrolled, any other count in a loop. */
 template <int DEG>
 static void launch_deg(int max_groups, const ClusterList& L, const NearArgs& a, int* queue, unsigned long long* acc,
-                       double* vir, int* status, cudaStream_t st)
+                       double* vir, int* status, int ctas_per_sm, cudaStream_t st)
 {
     if (a.n_explicit == 1)
-        launch_half<kNearGroup, DEG, 1>(max_groups, L, a, queue, acc, vir, status, st);
+        launch_half<kNearGroup, DEG, 1>(max_groups, L, a, queue, acc, vir, status, ctas_per_sm, st);
     else
-        launch_half<kNearGroup, DEG, -1>(max_groups, L, a, queue, acc, vir, status, st);
+        launch_half<kNearGroup, DEG, -1>(max_groups, L, a, queue, acc, vir, status, ctas_per_sm, st);
 }
 
 void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& a, int* queue,
-                 unsigned long long* acc, double* vir, int* status, cudaStream_t st)
+                 unsigned long long* acc, double* vir, int* status, int ctas_per_sm, cudaStream_t st)
 {
+#define USR_NEAR_DEG(D) \
+    case D: launch_deg<D>(max_groups, L, a, queue, acc, vir, status, ctas_per_sm, st); break;
     switch (deg) {
-        case 6: launch_deg<6>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 7: launch_deg<7>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 8: launch_deg<8>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 10: launch_deg<10>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 12: launch_deg<12>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 16: launch_deg<16>(max_groups, L, a, queue, acc, vir, status, st); break;
-        case 20: launch_deg<20>(max_groups, L, a, queue, acc, vir, status, st); break;
-        default: launch_deg<24>(max_groups, L, a, queue, acc, vir, status, st); break;
+        USR_NEAR_DEG(6)
+        USR_NEAR_DEG(7)
+        USR_NEAR_DEG(8)
+        USR_NEAR_DEG(10)
+        USR_NEAR_DEG(12)
+        USR_NEAR_DEG(16)
+        USR_NEAR_DEG(20)
+        default: launch_deg<24>(max_groups, L, a, queue, acc, vir, status, ctas_per_sm, st); break;
     }
+#undef USR_NEAR_DEG
 }
 
 void launch_pairs(int max_clusters, const ClusterList& L, const int* perm, const NearArgs& a, int* count,

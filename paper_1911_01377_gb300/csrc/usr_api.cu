@@ -87,7 +87,8 @@ struct usr_ctx {
     // host-buffer staging and inspection
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
     bool keep_parts = false;
-    bool inject_timeout = false;   // the next evaluation's first tensor-core pass waits on a barrier nothing completes
+    bool inject_timeout = false;
+    int near_ctas_per_sm = 0;      // persistent pair-kernel CTAs per SM (0: as many as fit)   // the next evaluation's first tensor-core pass waits on a barrier nothing completes
     bool parts_valid = false;
     // the far chain (spread, convolutions, psi mean) runs on `side`, a high-priority stream forked from and
     // joined back to the caller's stream, while the pair kernel runs on the caller's stream
@@ -710,7 +711,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     {
         NvtxRange r("usr: near pairs");
         usr::launch_near(c->max_groups, P.poly_deg, cluster_list(c), c->near, c->d_queue, c->d_nacc,
-                         c->vir ? c->d_vnear : nullptr, c->d_status, st);
+                         c->vir ? c->d_vnear : nullptr, c->d_status, c->near_ctas_per_sm, st);
         mark(2, st);
     }
     // join
@@ -792,6 +793,11 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(USR_ERR_CUDA);
     *out = c;
     return USR_OK;
+}
+
+void usr::set_near_ctas_per_sm(usr_ctx* c, int ctas_per_sm)
+{
+    if (c) c->near_ctas_per_sm = ctas_per_sm > 0 ? ctas_per_sm : 0;
 }
 
 usr_status usr::reconfigure_with_plan(usr_ctx* c, const Plan& P, cudaStream_t st)

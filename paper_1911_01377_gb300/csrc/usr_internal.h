@@ -221,7 +221,9 @@ int near_group_clusters();
 int near_units(int max_groups);
 int near_splits();
 void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& a, int* queue,
-                 unsigned long long* acc, double* vir, int* status, cudaStream_t st);
+                 unsigned long long* acc, double* vir, int* status, int ctas_per_sm, cudaStream_t st);
+/* At most ctas_per_sm persistent pair-kernel CTAs per SM for this context (0: as many as fit). */
+void set_near_ctas_per_sm(usr_ctx* c, int ctas_per_sm);
 void launch_pairs(int max_clusters, const ClusterList& L, const int* perm, const NearArgs& a, int* count,
                   unsigned long long* hash, int* status, cudaStream_t st);
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,

@@ -3,19 +3,18 @@
  * (the serving form; the paper itself evaluates one system at a time).
  *
  * Requests (one periodic system each: box, grid, cutoff, preset, charges in
- * host memory) are queued by usr_server_submit from any host thread.  A
- * worker thread admits them in arrival order onto slots; a slot is a context
- * (usr_ctx, its cell list, grids and tables resident on the device) plus its
- * own CUDA stream.  Admission needs a free slot and room in the device-memory
- * budget: a slot's context is re-targeted to the request with usr_reconfigure
- * (which reuses its buffers, allocating only when the request is larger than
- * anything the slot held before), and the bytes all slots hold may not exceed
- * the budget.  Requests that arrive while others run are admitted as soon as
- * a slot and memory free up, so evaluations of different systems overlap on
- * the device.  Each admitted request is enqueued on its slot's stream as host
- * -> device copy, the evaluation, device -> host copies, and an event;
- * completion is detected by polling the event, and the latency (submit to
- * results in host memory) is recorded.
+ * host memory) are queued by usr_server_submit from any host thread.  Every
+ * slot -- a context (usr_ctx: cell list, grids and tables resident on the
+ * device) with its own CUDA stream -- is served by its own host thread, which
+ * takes the next request in arrival order as soon as its slot is free, makes
+ * the request's FP64 plan, waits for room in the device-memory budget,
+ * re-targets its context to the request with usr_reconfigure (which reuses
+ * its buffers, allocating only when the request is larger than anything the
+ * slot held before), enqueues host -> device copy, evaluation and device ->
+ * host copies on its stream, and waits for them.  The host work of different
+ * requests (planning, table uploads, launches) therefore runs in parallel on
+ * the host cores, and their device work overlaps on the GPU.  The latency of a
+ * request is measured from submission to results in host memory.
  */
 #include <algorithm>
 #include <atomic>
@@ -38,7 +37,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
     long long ticket;
     usr_params params;
-    std::shared_ptr<usr::Plan> plan;     // made by the worker at admission
+    std::shared_ptr<usr::Plan> plan;     // made by the slot's thread after it takes the request
     double need = 0.0;                   // device bytes of a fresh context for it
     int n;
     const float* xyzq;
@@ -51,9 +50,10 @@ struct Slot {
     usr_ctx* ctx = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
-    bool busy = false;
-    double bytes = 0.0;          // device bytes the slot's context holds (it only grows)
-    Request req;
+    bool busy = false;           // a request is being prepared or evaluated on it
+    bool admitted = false;       // its request has its memory reserved and is being evaluated
+    double bytes = 0.0;          // device bytes the slot's context holds or has reserved (it only grows)
+    std::thread th;
 };
 
 struct Done {
@@ -72,8 +72,8 @@ struct usr_server {
     std::vector<Done> done;
     std::mutex mu;
     std::condition_variable cv;
-    std::thread worker;
-    std::atomic<bool> stop{false};
+    bool stop = false;
+    int admitted = 0;            // slots whose request passed admission and is being evaluated
     long long next_ticket = 0;
     long long completed = 0;
     long long submitted = 0;
@@ -83,8 +83,8 @@ struct usr_server {
 
 namespace {
 
-/* Enqueue a request on a free slot (worker thread; the queue lock is not held). */
-usr_status launch(usr_server* s, Slot& sl, const Request& r)
+/* Re-target the slot's context to the request and enqueue its evaluation (no server lock held). */
+usr_status launch(Slot& sl, const Request& r)
 {
     usr_status st;
     if (!sl.ctx) {
@@ -92,18 +92,13 @@ usr_status launch(usr_server* s, Slot& sl, const Request& r)
     } else if ((st = usr::reconfigure_with_plan(sl.ctx, *r.plan, sl.st)) != USR_OK) {
         return st;
     }
-    usr_plan_info info;
-    usr_info(sl.ctx, &info);
-    sl.bytes = std::max(sl.bytes, info.device_bytes);
     if (r.n > 0 && (st = usr_eval_host_async(sl.ctx, r.n, r.xyzq, r.out, r.energy, sl.st)) != USR_OK) return st;
     if (r.n == 0 && r.energy) std::memset(r.energy, 0, 4 * sizeof(double));
     if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return USR_ERR_CUDA;
-    sl.req = r;
-    sl.busy = true;
     return USR_OK;
 }
 
-/* Plan a queued request once (the worker keeps the plan with the request). */
+/* Plan a request (the slot thread's host work before admission). */
 void plan_request(Request& r)
 {
     if (r.plan) return;
@@ -111,117 +106,99 @@ void plan_request(Request& r)
     r.need = usr::make_plan(&r.params, r.plan.get()) == USR_OK ? usr::plan_device_bytes(*r.plan) : -1.0;
 }
 
-/* Free the contexts of idle slots (all but `keep`): the only way held memory shrinks. */
+double held(const usr_server* s)
+{
+    double h = 0.0;
+    for (const auto& sl : s->slots) h += sl.bytes;
+    return h;
+}
+
+/*
+ * Free the contexts of slots other than `keep` that evaluate nothing (idle, or holding a request that
+ * still waits for admission: such a slot touches its context only once admitted); lock held.  This is
+ * the only way held memory shrinks.
+ */
 void release_idle(usr_server* s, int keep)
 {
     for (size_t i = 0; i < s->slots.size(); ++i) {
         Slot& sl = s->slots[i];
-        if ((int)i == keep || sl.busy || !sl.ctx) continue;
+        if ((int)i == keep || sl.admitted || !sl.ctx) continue;
         usr_destroy(sl.ctx);
         sl.ctx = nullptr;
         sl.bytes = 0.0;
     }
 }
 
-void worker_loop(usr_server* s)
+void slot_loop(usr_server* s, int idx)
 {
     cudaSetDevice(s->device);
+    Slot& sl = s->slots[idx];
     const double budget = s->prm.hbm_budget_bytes;
+    std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        bool progressed = false;
-        // completions
-        for (auto& sl : s->slots) {
-            if (!sl.busy) continue;
-            const cudaError_t q = cudaEventQuery(sl.done);
-            if (q == cudaErrorNotReady) continue;
-            usr_status st = q == cudaSuccess ? usr_last_device_status(sl.ctx) : USR_ERR_CUDA;
-            if (q != cudaSuccess) cudaGetLastError();
-            const double ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t_submit).count();
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->done.push_back({sl.req.ticket, ms, st});
-            ++s->completed;
-            sl.busy = false;
-            progressed = true;
+        s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+        if (s->stop) {                                       // shutting down: cancel what waits
+            for (const auto& q : s->queue) s->done.push_back({q.ticket, 0.0, USR_ERR_ARG});
+            s->completed += (long long)s->queue.size();
+            s->queue.clear();
             s->cv.notify_all();
+            break;
         }
-        // admissions, in arrival order
-        while (true) {
-            Request r;
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                if (s->queue.empty()) break;
-                if (s->stop) {                                     // shutting down: cancel what waits
-                    for (const auto& q : s->queue) s->done.push_back({q.ticket, 0.0, USR_ERR_ARG});
-                    s->completed += (long long)s->queue.size();
-                    s->queue.clear();
-                    s->cv.notify_all();
-                    break;
+        Request r = s->queue.front();                        // arrival order
+        s->queue.pop_front();
+        sl.busy = true;
+        lk.unlock();
+        plan_request(r);                                     // in parallel with the other slots
+        lk.lock();
+        // admission by memory: re-targeted to r, the slot holds at most max(its bytes, r's need)
+        usr_status st = r.need < 0.0 ? USR_ERR_BOX : (r.need > budget ? USR_ERR_OOM : USR_OK);
+        while (st == USR_OK) {
+            const double after = held(s) - sl.bytes + std::max(sl.bytes, r.need);
+            if (after <= budget) break;
+            if (s->admitted == 0) {
+                // nothing is evaluated, so waiting frees nothing: release the other slots' contexts,
+                // then if needed this one
+                release_idle(s, idx);
+                if (held(s) - sl.bytes + std::max(sl.bytes, r.need) > budget && sl.ctx) {
+                    usr_destroy(sl.ctx);
+                    sl.ctx = nullptr;
+                    sl.bytes = 0.0;
                 }
-                plan_request(s->queue.front());
-                r = s->queue.front();
-            }
-            const double need = r.need;
-            // a free slot, preferring the one holding the most (its buffers are the likeliest to fit)
-            int best = -1;
-            for (size_t i = 0; i < s->slots.size(); ++i) {
-                const Slot& sl = s->slots[i];
-                if (sl.busy) continue;
-                if (best < 0 || sl.bytes > s->slots[best].bytes) best = (int)i;
-            }
-            if (best < 0) break;                                   // no free slot
-            // a slot re-targeted to the request holds at most its current bytes plus the request's
-            // own need (buffers grow to the larger of the two), so admit only if that fits
-            double held = 0.0;
-            bool any_busy = false;
-            for (const auto& sl : s->slots) {
-                held += sl.bytes;
-                any_busy = any_busy || sl.busy;
-            }
-            double best_growth = need;
-            if (need >= 0.0 && need <= budget && held + best_growth > budget && !any_busy) {
-                // nothing runs, so waiting frees nothing: release idle slots, then if needed the chosen one
-                release_idle(s, best);
-                held = s->slots[best].bytes;
-                if (held + best_growth > budget) {
-                    release_idle(s, -1);
-                    held = 0.0;
-                }
-            }
-            if (need < 0.0 || need > budget || held + best_growth > budget) {
-                if (need >= 0.0 && need <= budget) break;          // wait for memory
-                std::lock_guard<std::mutex> lk(s->mu);             // can never fit: fail it
-                s->queue.pop_front();
-                s->done.push_back({r.ticket, 0.0, need < 0.0 ? USR_ERR_BOX : USR_ERR_OOM});
-                ++s->completed;
-                s->cv.notify_all();
                 continue;
             }
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                s->queue.pop_front();
-            }
-            Slot& sl = s->slots[best];
-            const usr_status st = launch(s, sl, r);
-            held = 0.0;
-            for (const auto& x : s->slots) held += x.bytes;
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->held_bytes = held;
-            if (st != USR_OK) {
-                if (s->first_error == USR_OK) s->first_error = st;
-                s->done.push_back({r.ticket, 0.0, st});
-                ++s->completed;
-                sl.busy = false;
-                s->cv.notify_all();
-            }
-            progressed = true;
+            s->cv.wait(lk);                                  // until another request completes
         }
-        std::unique_lock<std::mutex> lk(s->mu);
-        if (s->stop && s->queue.empty()) {
-            bool any = false;
-            for (const auto& sl : s->slots) any = any || sl.busy;
-            if (!any) break;
+        if (st == USR_OK) {
+            sl.bytes = std::max(sl.bytes, r.need);           // reserved before the lock is released
+            sl.admitted = true;
+            ++s->admitted;
         }
-        if (!progressed) s->cv.wait_for(lk, std::chrono::microseconds(20));
+        lk.unlock();
+        usr_status lst = USR_OK;
+        if (st == USR_OK) {
+            lst = launch(sl, r);
+            st = lst;
+            if (st == USR_OK) {
+                st = cudaEventSynchronize(sl.done) == cudaSuccess ? usr_last_device_status(sl.ctx) : USR_ERR_CUDA;
+                if (st == USR_ERR_CUDA) cudaGetLastError();
+            }
+        }
+        const double ms = std::chrono::duration<double, std::milli>(Clock::now() - r.t_submit).count();
+        double ctx_bytes = 0.0;
+        if (sl.ctx) {
+            usr_plan_info info;
+            if (usr_info(sl.ctx, &info) == USR_OK) ctx_bytes = info.device_bytes;
+        }
+        lk.lock();
+        sl.bytes = sl.ctx ? std::max(sl.bytes, ctx_bytes) : 0.0;
+        s->held_bytes = held(s);
+        if (lst != USR_OK && s->first_error == USR_OK) s->first_error = lst;
+        s->done.push_back({r.ticket, ms, st});
+        ++s->completed;
+        if (sl.admitted) --s->admitted;
+        sl.admitted = false;
+        sl.busy = false;
+        s->cv.notify_all();
     }
 }
 
@@ -255,7 +232,7 @@ extern "C" usr_status usr_server_create(const usr_server_params* p, usr_server**
             return USR_ERR_CUDA;
         }
     }
-    s->worker = std::thread(worker_loop, s);
+    for (int i = 0; i < (int)s->slots.size(); ++i) s->slots[i].th = std::thread(slot_loop, s, i);
     *out = s;
     return USR_OK;
 }
@@ -327,7 +304,8 @@ extern "C" void usr_server_destroy(usr_server* s)
         s->stop = true;
     }
     s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (auto& sl : s->slots)
+        if (sl.th.joinable()) sl.th.join();
     for (auto& sl : s->slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         if (sl.ctx) usr_destroy(sl.ctx);

@@ -189,6 +189,11 @@ def usr_eval_host(ctx: int, n: int, xyzq_ptr: int, out_ptr: int, energy_ptr: Opt
     _check(lib().usr_eval_host(ctx, int(n), xyzq_ptr, out_ptr, energy_ptr, _stream_ptr(stream)), "usr_eval_host")
 
 
+def usr_eval_host_async(ctx: int, n: int, xyzq_ptr: int, out_ptr: int, energy_ptr: Optional[int], stream=None):
+    _check(lib().usr_eval_host_async(ctx, int(n), xyzq_ptr, out_ptr, energy_ptr, _stream_ptr(stream)),
+           "usr_eval_host_async")
+
+
 def usr_last_device_status(ctx: int) -> int:
     return lib().usr_last_device_status(ctx)
 
