@@ -43,6 +43,9 @@
 #ifndef USR_NEAR_GI
 #define USR_NEAR_GI 4
 #endif
+#ifndef USR_NEAR_MINB
+#define USR_NEAR_MINB 4     // CTAs of 128 threads per SM the register budget is set for
+#endif
 #ifndef USR_NEAR_NEWTON
 #define USR_NEAR_NEWTON 0
 #endif
@@ -114,8 +117,8 @@ struct NearVir {
 };
 
 /*
- * One 8 x 8 step between i-cluster I and the lane's j atom (position already
- * shifted to the image, xj/yj/zj duplicated into both halves).  Padding rows
+ * One 8 x 8 step between i-cluster I and the lane's j atom (xj/yj/zj: minus its
+ * position shifted to the image, duplicated into both halves).  Padding rows
  * never pass the distance test: as j atoms they sit near -1e6 (cpos), as i atoms
  * near +1e7 (replaced when the group is loaded).  TRI: the j-cluster is I
  * itself, only pairs with j after i count (tri_a / tri_b for halves a / b).
@@ -124,7 +127,7 @@ template <int DEG, int NEXP, bool VIR, bool TRI>
 __device__ __forceinline__ void pair_step(const NearArgs& a, NearI& I, f2 xj, f2 yj, f2 zj, float qj, bool tri_a,
                                           bool tri_b, f2& fjx, f2& fjy, f2& fjz, f2& fjp, NearVir& V)
 {
-    const f2 dx = sub2(I.x, xj), dy = sub2(I.y, yj), dz = sub2(I.z, zj);
+    const f2 dx = add2(I.x, xj), dy = add2(I.y, yj), dz = add2(I.z, zj);
     const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     const float r2a = r2.x, r2b = r2.y;
     bool ina = r2a < a.rc2, inb = r2b < a.rc2;
@@ -138,24 +141,25 @@ __device__ __forceinline__ void pair_step(const NearArgs& a, NearI& I, f2 xj, f2
     const f2 u = pk(ua, ub);
     f2 ri = pk(rsqrt_ftz(ua), rsqrt_ftz(ub));
     if (USR_NEAR_NEWTON) ri = mul2(ri, fma2(mul2(mul2(u, ri), ri), dup(-0.5f), dup(1.5f)));
+    // pn = -F(u) and its derivative chain, so that N = 1/r + pn needs no sign change
     const f2 s = fma2(u, dup(a.two_over_rc2), dup(-1.0f));
-    f2 p = dup(a.poly[DEG]), dp = p;
-    p = fma2(p, s, dup(a.poly[DEG - 1]));
+    f2 pn = dup(a.npoly[DEG]), dpn = pn;
+    pn = fma2(pn, s, dup(a.npoly[DEG - 1]));
     #pragma unroll
     for (int d = DEG - 2; d >= 0; --d) {
-        dp = fma2(dp, s, p);
-        p = fma2(p, s, dup(a.poly[d]));
+        dpn = fma2(dpn, s, pn);
+        pn = fma2(pn, s, dup(a.npoly[d]));
     }
-    f2 d2 = mul2(dp, dup(2.0f * a.two_over_rc2));                        // 2 dF/du
+    f2 d2 = mul2(dpn, dup(a.nd2fac));                                     // 2 dF/du
     const int nexp = NEXP >= 0 ? NEXP : a.n_explicit;
     #pragma unroll
     for (int e = 0; e < nexp; ++e) {
         const f2 t = mul2(u, dup(a.el2[e]));
-        const f2 gg = mul2(pk(exp2_ftz(t.x), exp2_ftz(t.y)), dup(a.ea[e]));
-        p = add2(p, gg);
-        d2 = fma2(gg, dup(a.ne2[e]), d2);
+        const f2 ggn = mul2(pk(exp2_ftz(t.x), exp2_ftz(t.y)), dup(a.nea[e]));   // minus the Gaussian
+        pn = add2(pn, ggn);
+        d2 = fma2(ggn, dup(a.nne2[e]), d2);
     }
-    const f2 nr = sub2(ri, p);                                            // N(r)
+    const f2 nr = add2(ri, pn);                                           // N(r) = 1/r - F
     const f2 g = fma2(mul2(ri, ri), ri, d2);                              // -N'(r) / r
     const float qia = I.q.x, qib = I.q.y;
     const f2 Qj = pk(ina ? qj : 0.f, inb ? qj : 0.f);
@@ -279,7 +283,8 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
                 const int jcl = jb + t;
                 const unsigned int mk = __shfl_sync(0xffffffffu, m, t);
                 const float* pj = cf + jcl * 32 + joff;
-                const float xj = __fadd_rn(pj[0], sx), yj = __fadd_rn(pj[2], sy), zj = __fadd_rn(pj[4], sz);
+                // minus the image position, -(x_j + shift): d = x_i + that, the same number as x_i - (x_j + shift)
+                const float xj = -__fadd_rn(pj[0], sx), yj = -__fadd_rn(pj[2], sy), zj = -__fadd_rn(pj[4], sz);
                 const float qj = pj[6];
                 const int sj = L.cidx[jcl * 8 + jl];
                 const f2 xj2 = dup(xj), yj2 = dup(yj), zj2 = dup(zj);
@@ -368,7 +373,7 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
  * writes its pair virial to vir[6 u ..].
  */
 template <int GI, int DEG, int NEXP, bool VIR>
-__global__ void __launch_bounds__(128, GI >= 4 ? 4 : 5) k_near_half(ClusterList L, NearArgs a, int* __restrict__ queue,
+__global__ void __launch_bounds__(128, USR_NEAR_MINB) k_near_half(ClusterList L, NearArgs a, int* __restrict__ queue,
                                                                     unsigned long long* __restrict__ acc,
                                                                     double* __restrict__ vir, int* __restrict__ status)
 {
@@ -551,6 +556,7 @@ void launch_near(int max_groups, int deg, const ClusterList& L, const NearArgs& 
 #define USR_NEAR_DEG(D) \
     case D: launch_deg<D>(max_groups, L, a, queue, acc, vir, status, ctas_per_sm, st); break;
     switch (deg) {
+        USR_NEAR_DEG(5)
         USR_NEAR_DEG(6)
         USR_NEAR_DEG(7)
         USR_NEAR_DEG(8)

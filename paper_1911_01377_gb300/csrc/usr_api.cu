@@ -554,7 +554,15 @@ void fill_args(usr_ctx* c)
         a.el2[e] = (float)(-P.einv[e] * 1.4426950408889634);    // log2(e)
         a.ne2[e] = (float)(-2.0 * P.einv[e]);
     }
-    for (int d = 0; d <= usr::kMaxPolyDeg; ++d) a.poly[d] = (float)P.poly[d];
+    for (int d = 0; d <= usr::kMaxPolyDeg; ++d) {
+        a.poly[d] = (float)P.poly[d];
+        a.npoly[d] = -a.poly[d];
+    }
+    for (int e = 0; e < usr::kMaxExplicit; ++e) {
+        a.nea[e] = -a.ea[e];
+        a.nne2[e] = -a.ne2[e];
+    }
+    a.nd2fac = -2.0f * a.two_over_rc2;
     usr::GridArgs& g = c->grid;
     std::memset(&g, 0, sizeof(g));
     g.box = c->boxf;

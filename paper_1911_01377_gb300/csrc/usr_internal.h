@@ -123,6 +123,12 @@ struct NearArgs {
     float el2[kMaxExplicit];   // -einv log2(e): exp(-u einv) = 2^(u el2)
     float ne2[kMaxExplicit];   // -2 einv: factor of 2 dF/du
     float poly[kMaxPolyDeg + 1];
+    // the same with their signs flipped, for the pair kernel's negated form of F (-F and its
+    // derivative accumulate with additions only)
+    float npoly[kMaxPolyDeg + 1];
+    float nea[kMaxExplicit];   // -ea
+    float nne2[kMaxExplicit];  // -ne2
+    float nd2fac;              // -2 * two_over_rc2: 2 dF/du from d(-F)/ds
 };
 
 /*

@@ -400,17 +400,19 @@ usr_status make_plan(const usr_params* pp, Plan* out)
         }
     }
     // the pair kernel evaluates F in FP32 (relative rounding ~6e-8): a fit error
-    // well below that is enough
+    // below that is enough.  Value: 5e-9 of F(0).  Derivative: 2e-6 of max |dF/du|,
+    // which for the C1 presets is a few 1e-10 absolute, below the FP32 rounding of
+    // the 1/r^3 term it is added to at any r < r_c (degree 5 for C1 b = 2)
     // The fit depends on the series and r_c only (not on the box): systems that
     // share them (a serving stream) reuse it from a small cache.
     double ev = 1.0, ed = 1.0;
     if (!fit_cache_get(P, &ev)) {
-        static const int kDegs[] = {6, 7, 8, 10, 12, 16, 20, 24};
+        static const int kDegs[] = {5, 6, 7, 8, 10, 12, 16, 20, 24};
         P.poly_deg = 0;
         for (int D : kDegs) {
             fit_poly(P, D, P.poly, &ev, &ed);
             P.poly_deg = D;
-            if (ev < 2e-9 && ed < 1e-7) break;
+            if (ev < 5e-9 && ed < 2e-6) break;
         }
         for (int i = P.poly_deg + 1; i <= kMaxPolyDeg; ++i) P.poly[i] = 0.0;
         fit_cache_put(P, ev);

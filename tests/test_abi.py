@@ -59,7 +59,8 @@ def test_plan_matches_closed_forms(libusr, tables, r_c):
     assert abs(info.trunc_bound / S.trunc_bound(N, ser.b, r_c / ser.r0, max(box)) - 1.0) < 1e-9
     assert list(info.cells) == [int(math.floor(L / r_c)) for L in box]
     assert list(info.h) == [L / n for L, n in zip(box, grid)]
-    assert info.poly_max_err < 1e-9
+    # the pair kernel's polynomial for the wide terms of F: within 5e-9 of F(0), below FP32 rounding
+    assert info.poly_max_err < 5e-9
 
 
 def test_plan_rejects_unsupported_input(libusr):
