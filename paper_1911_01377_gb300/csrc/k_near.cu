@@ -44,7 +44,8 @@
 #define USR_NEAR_GI 4
 #endif
 #ifndef USR_NEAR_MINB
-#define USR_NEAR_MINB 4     // CTAs of 128 threads per SM the register budget is set for
+#define USR_NEAR_MINB 5     // CTAs of 128 threads per SM the register budget is set for (96 registers:
+                            // 20 warps per SM, 122 us at r_c = 10 A on the slab against 133 us with 16)
 #endif
 #ifndef USR_NEAR_NEWTON
 #define USR_NEAR_NEWTON 0
