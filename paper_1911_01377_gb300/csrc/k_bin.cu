@@ -8,7 +8,7 @@
  *   place       scatter caller indices into their cell's range
  *   cell_sort   order each cell's atoms by caller index (a stable, run-to-run
  *               deterministic order) and gather the sorted float4 rows
- *   cell_build  the same sort fused with the pair kernel's 8-atom clusters
+ *   clusters    the pair kernel's 8-atom clusters, built from the sorted list
  *
  * Predicate (per axis, RN rounding, no contraction):
  *   k = floorf(x * invL); xw = fmaf(-k, L, x); if (xw < 0) xw += L;
@@ -218,27 +218,26 @@ __device__ __forceinline__ int morton_key(float4 p, float ox, float oy, float oz
 }
 
 /*
- * The cell sort and the clusters in one pass, one CTA per cell: first the
- * cell's atoms in caller-index order (perm, sorted rows) with the Morton key
- * of each sorted row, then the cluster order from the keys (as above).  Also
- * the first cluster of each of the cell's groups of gcl clusters, and the
- * cell's rows of the pair kernel's fixed-point accumulators set to zero.
+ * The clusters of one cell per CTA, from the sorted cell list (k_cell_sort):
+ * Morton order as above, the padded paired layout, each cluster's bounding
+ * box; also the first cluster of each of the cell's groups of gcl clusters,
+ * and the cell's rows of the pair kernel's fixed-point accumulators set to
+ * zero.  A separate kernel from the sort, so that the far part, which needs
+ * only the sorted list, can start beside it on another stream.
  */
-__global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restrict__ start,
-                                                             const int* __restrict__ pstart,
-                                                             const int* __restrict__ gfull,
-                                                             const int* __restrict__ gpart, int gcl,
-                                                             const int* __restrict__ unsorted,
-                                                             const float4* __restrict__ wpos, BoxF b,
-                                                             int* __restrict__ perm, float4* __restrict__ spos,
-                                                             int* __restrict__ key, float4* __restrict__ cpos,
-                                                             int* __restrict__ cidx, int* __restrict__ ccell,
-                                                             float4* __restrict__ bblo, float4* __restrict__ bbhi,
-                                                             int* __restrict__ gfirst,
-                                                             unsigned long long* __restrict__ acc, int n,
-                                                             int max_slots, int max_groups, int* __restrict__ status)
+__global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __restrict__ start,
+                                                                const int* __restrict__ pstart,
+                                                                const int* __restrict__ gfull,
+                                                                const int* __restrict__ gpart, int gcl, BoxF b,
+                                                                const float4* __restrict__ spos,
+                                                                int* __restrict__ key, float4* __restrict__ cpos,
+                                                                int* __restrict__ cidx, int* __restrict__ ccell,
+                                                                float4* __restrict__ bblo, float4* __restrict__ bbhi,
+                                                                int* __restrict__ gfirst,
+                                                                unsigned long long* __restrict__ acc, int n,
+                                                                int max_slots, int max_groups,
+                                                                int* __restrict__ status)
 {
-    __shared__ int v[kSortMax];
     __shared__ int ks[kSortMax];
     const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
@@ -264,21 +263,10 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_build(const int* __restri
             for (int e = threadIdx.x; e < 2 * m; e += kSortThreads) a2[e] = make_ulonglong2(0ull, 0ull);
         }
     }
-    if (in_smem)
-        for (int e = threadIdx.x; e < m; e += kSortThreads) v[e] = unsorted[s0 + e];
-    __syncthreads();
-    const int* src = in_smem ? v : unsorted + s0;
     int* kk = in_smem ? ks : key + s0;
-    for (int e = threadIdx.x; e < m; e += kSortThreads) {
-        const int x = src[e];
-        int r = 0;
-        for (int f = 0; f < m; ++f) r += src[f] < x;
-        if (!USR_IN_BOUNDS(s0 + r, n, status) || !USR_IN_BOUNDS(x, n, status)) continue;
-        const float4 p = wpos[x];
-        perm[s0 + r] = x;
-        spos[s0 + r] = p;
-        kk[r] = morton_key(p, ox, oy, oz, kx, ky, kz);
-    }
+    if (!USR_IN_BOUNDS(s0 + m - 1, n, status)) return;
+    // cluster order: Morton code of each atom on an 8 x 8 x 8 lattice inside the cell, ties by sorted index
+    for (int e = threadIdx.x; e < m; e += kSortThreads) kk[e] = morton_key(spos[s0 + e], ox, oy, oz, kx, ky, kz);
     __syncthreads();
     for (int e = threadIdx.x; e < m; e += kSortThreads) {
         const int ke = kk[e];
@@ -335,12 +323,10 @@ cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int*
     return cudaGetLastError();
 }
 
-/* The pair kernels' full cell list: counts, scan, placement, then the sort and the clusters fused per cell. */
-void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                      float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
-                      int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
-                      float4* bbhi, unsigned long long* near_acc, int max_clusters, int max_groups, int* status,
-                      cudaStream_t st)
+/* The sorted cell list: counts, scan (with the pair kernel's group counts), placement, per-cell sort. */
+void launch_bin_sorted(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                       float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* queue, int* unsorted,
+                       int* perm, float4* spos, int* status, cudaStream_t st)
 {
     const int gcl = near_group_clusters();
     cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
@@ -348,10 +334,18 @@ void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* 
     k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
     k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, gfull, gpart, gcl, queue);
     k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted, status);
-    // slot[] is free after placement: it holds the Morton keys of cells too large for shared memory
-    k_cell_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, gfull, gpart, gcl, unsorted, wpos, b, perm, spos,
-                                                  slot, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc, n,
-                                                  8 * max_clusters, max_groups, status);
+    k_cell_sort<<<ncell, kSortThreads, 0, st>>>(n, cell_start, unsorted, wpos, perm, spos, status);
+}
+
+/* The pair kernels' clusters from the sorted cell list (slot[] of launch_bin_sorted is reused for keys). */
+void launch_clusters(int n, const BoxF& b, int ncell, const int* cell_start, const int* pstart, const int* gfull,
+                     const int* gpart, int* gfirst, const float4* spos, int* key, float4* cpos, int* cidx,
+                     int* ccell, float4* bblo, float4* bbhi, unsigned long long* near_acc, int max_clusters,
+                     int max_groups, int* status, cudaStream_t st)
+{
+    k_cluster_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, gfull, gpart, near_group_clusters(), b, spos,
+                                                     key, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc, n,
+                                                     8 * max_clusters, max_groups, status);
 }
 
 }  // namespace usr

@@ -5,7 +5,7 @@
  * over all j != i and periodic images.
  *
  * Half-list cluster-pair kernel (k_near_half).  Each cell's atoms come in
- * 8-atom spatial clusters (k_cell_build), and the clusters of a cell in groups
+ * 8-atom spatial clusters (k_cluster_build), and the clusters of a cell in groups
  * of GI consecutive clusters.  One warp owns one group and walks the j-clusters
  * of its own cell (from the group's first cluster on) and of the 13 neighbour
  * cells whose offset (dz, dy, dx) is lexicographically positive, so that every
@@ -370,7 +370,7 @@ __device__ __forceinline__ void near_unit(const ClusterList& L, const NearArgs& 
  * Persistent warps: each takes work units (group, neighbour range) from a queue counter (zeroed by
  * the cell-list scan), full groups first and the partial ones last, until none is left.  The
  * accumulation is integer, so results do not depend on which warp takes which unit.  acc: 4
- * fixed-point accumulators (Fx, Fy, Fz, phi) per sorted atom, zeroed by k_cell_build.  VIR: unit u
+ * fixed-point accumulators (Fx, Fy, Fz, phi) per sorted atom, zeroed by k_cluster_build.  VIR: unit u
  * writes its pair virial to vir[6 u ..].
  */
 template <int GI, int DEG, int NEXP, bool VIR>

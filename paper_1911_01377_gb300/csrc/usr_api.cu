@@ -584,13 +584,26 @@ usr_status check_device(const usr_ctx* c)
     return dev == c->device ? USR_OK : USR_ERR_ARG;
 }
 
-/* Cell list (canonical sorted order) and the 8-atom clusters built from it. */
+/* Cell list in canonical sorted order (cell ids, counting sort, order by caller index within a cell). */
+void bin_sorted(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
+{
+    usr::launch_bin_sorted(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
+                           c->d_cell_start, c->d_pstart, c->d_gfull, c->d_gpart, c->d_queue, c->d_unsorted, c->d_perm,
+                           c->d_spos, c->d_status, st);
+}
+
+/* The pair kernels' 8-atom clusters, groups and zeroed accumulators, from the sorted cell list. */
+void build_clusters(usr_ctx* c, int n, cudaStream_t st)
+{
+    usr::launch_clusters(n, c->boxf, c->ncell, c->d_cell_start, c->d_pstart, c->d_gfull, c->d_gpart, c->d_gfirst,
+                         c->d_spos, c->d_slot, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_nacc,
+                         c->max_clusters, c->max_groups, c->d_status, st);
+}
+
 void bin_and_cluster(usr_ctx* c, int n, const float4* xyzq, cudaStream_t st)
 {
-    usr::launch_bin_cells(n, xyzq, c->boxf, c->ncell, c->d_count, c->d_cell_of, c->d_slot, c->d_wpos,
-                          c->d_cell_start, c->d_pstart, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_unsorted, c->d_perm,
-                          c->d_spos, c->d_cpos, c->d_cidx, c->d_ccell, c->d_bblo, c->d_bbhi, c->d_nacc,
-                          c->max_clusters, c->max_groups, c->d_status, st);
+    bin_sorted(c, n, xyzq, st);
+    build_clusters(c, n, st);
 }
 
 usr::ClusterList cluster_list(const usr_ctx* c)
@@ -681,13 +694,17 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     mark(0, st);
     {
         NvtxRange r("usr: cell list");
-        bin_and_cluster(c, n, xyzq, st);
+        bin_sorted(c, n, xyzq, st);
     }
-    mark(1, st);
-    // fork: the far chain on the side stream (first, so that its few large CTAs are placed before the
-    // pair kernel's many small ones fill the SMs), the pair kernel on the caller's stream
+    // fork: the far chain needs only the sorted cell list, so it starts on the side stream while the caller's
+    // stream builds the pair kernel's clusters and then runs the pair kernel
     if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev_fork, 0) != cudaSuccess)
         return USR_ERR_CUDA;
+    {
+        NvtxRange r("usr: clusters");
+        build_clusters(c, n, st);
+    }
+    mark(1, st);
     cudaStream_t sd = c->side;
     {
         NvtxRange r("usr: far chain (spread, convolutions, psi mean)");

@@ -133,7 +133,7 @@ struct NearArgs {
 
 /*
  * The cell list as the pair kernels read it: 8-slot clusters (paired layout,
- * see k_cell_build) with their caller-sorted indices (-1 for padding rows),
+ * see k_cluster_build) with their caller-sorted indices (-1 for padding rows),
  * cells, bounding boxes, per-cell padded slot starts, and the groups of
  * consecutive clusters of one cell that one warp of the half-list kernel owns
  * (per-cell group starts, first cluster of each group).
@@ -215,11 +215,15 @@ struct ConvTcMaps {
 cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                        float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
                        int* status, cudaStream_t st);
-void launch_bin_cells(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
-                      float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* gfirst, int* queue,
-                      int* unsorted, int* perm, float4* spos, float4* cpos, int* cidx, int* ccell, float4* bblo,
-                      float4* bbhi, unsigned long long* near_acc, int max_clusters, int max_groups, int* status,
-                      cudaStream_t st);
+/* The sorted cell list (cell ids, counting sort, per-cell order by caller index); then the pair kernels'
+   clusters built from it (they may run on different streams, the second after the first). */
+void launch_bin_sorted(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
+                       float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* queue, int* unsorted,
+                       int* perm, float4* spos, int* status, cudaStream_t st);
+void launch_clusters(int n, const BoxF& b, int ncell, const int* cell_start, const int* pstart, const int* gfull,
+                     const int* gpart, int* gfirst, const float4* spos, int* key, float4* cpos, int* cidx,
+                     int* ccell, float4* bblo, float4* bbhi, unsigned long long* near_acc, int max_clusters,
+                     int max_groups, int* status, cudaStream_t st);
 /* Upper bound of the half-list kernel's groups for n atoms in ncell cells; clusters per group. */
 int near_max_groups(int n, int ncell);
 int near_group_clusters();
