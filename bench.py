@@ -53,9 +53,10 @@ FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x
 # algorithmic flops of one unordered pair inside r_c (the survey's 30-50 flop estimate of the pair
 # arithmetic, its midpoint), the unit of the pair kernel's roofline
 NEAR_FLOPS_PER_PAIR = 40
-# DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over the evaluation
-# launches of one ncu capture; None whenever the pair kernel has changed since that capture
-NEAR_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over its six launches (one
+# per cutoff) in one ncu capture of `bench.py --steps 1 --warmup 3 --serve-systems 0 --no-scale`; None whenever
+# the pair kernel has changed since that capture
+NEAR_TRAFFIC_BYTES = 3.718e6
 # forms: (name, conv, spread_points, spread_sigma_over_h)
 CHOSEN = ("bf16x3_gse8", 2, 8, 0.83)
 COMPARATORS = (("fp32_gse8", 0, 8, 0.83), ("fp32_tight12", 0, 12, 1.0))
@@ -220,8 +221,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWEEP):
-    """Device-time `steps` sweeps of one form; returns (total ms, per-stage ms sums, contexts, outs, ens)."""
+def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWEEP, stage_steps=3):
+    """Device-time `steps` sweeps of one form with events around the pair kernel only (profiling level 2,
+    so its launch duration is measured inside the timed region); then `stage_steps` more sweeps with every
+    stage boundary recorded, outside the timed region, for the stage breakdown.  Returns (total ms, per-stage
+    ms means, pair-kernel ms sums of the timed steps, contexts, outs, ens)."""
     name, conv, P, ratio = form
     ctxs = [usr.USeries(w.box, w.grid, r_c, "C1_B2", max_atoms=w.n, conv=conv, spread_points=P,
                         spread_sigma_over_h=ratio) for r_c in cutoffs]
@@ -240,8 +244,8 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWE
         st = usr.usr_last_device_status(c.ctx)
         if st != 0:
             raise usr.UsrError(st, f"device status after warm-up ({name})")
-        usr.usr_set_profiling(c.ctx, True)
-    stage = [[0.0] * usr.USR_NSTAGES for _ in cutoffs]
+        usr.usr_set_profiling(c.ctx, 2)
+    near = [0.0 for _ in cutoffs]
     total = 0.0
     for k in range(steps):
         flush.fill_(float(k % 7))
@@ -253,11 +257,20 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWE
         e1.synchronize()
         total += e0.elapsed_time(e1)
         for i, c in enumerate(ctxs):
-            for s, v in enumerate(usr.usr_stage_times(c.ctx)):
-                stage[i][s] += v
+            near[i] += usr.usr_stage_times(c.ctx)[1]
+    stage = [[0.0] * usr.USR_NSTAGES for _ in cutoffs]
     for c in ctxs:
-        usr.usr_set_profiling(c.ctx, False)
-    return total, stage, ctxs, outs, ens
+        usr.usr_set_profiling(c.ctx, 1)
+    for k in range(stage_steps):
+        flush.fill_(float(k % 7))
+        step()
+        torch.cuda.synchronize()
+        for i, c in enumerate(ctxs):
+            for s_, v in enumerate(usr.usr_stage_times(c.ctx)):
+                stage[i][s_] += v / stage_steps
+    for c in ctxs:
+        usr.usr_set_profiling(c.ctx, 0)
+    return total, stage, near, ctxs, outs, ens
 
 
 SCALE_FORMS = (CHOSEN, ("tf32x3_gse8", 1, 8, 0.83), COMPARATORS[0], COMPARATORS[1])
@@ -272,9 +285,9 @@ def run_scale(usr, torch, steps, warmup, flush, stream):
     x = torch.from_numpy(w.xyzq).to(flush.device)
     forms = {}
     for form in SCALE_FORMS:
-        tms, stage, cc, _, _ = _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=(10.0,))
+        tms, stage, _, cc, _, _ = _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=(10.0,))
         forms[form[0]] = {"value": w.n * steps / (tms / 1e3), "unit": UNIT, "ms_per_eval": tms / steps,
-                          "stage_ms": {k: v / steps for k, v in zip(usr.STAGES, stage[0])}}
+                          "stage_ms": dict(zip(usr.STAGES, stage[0]))}
         for c in cc:
             c.close()
     return {"workload": f"water_1m: {w.n} charges (354933 3-site waters), cubic L=220 A, 176^3 grid, "
@@ -400,8 +413,8 @@ def run_gpu(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    total_ms, stage_ms, ctxs, outs, ens = _time_form(usr, torch, w, x, CHOSEN, args.steps, args.warmup, flush,
-                                                     stream)
+    total_ms, stage_ms, near_ms, ctxs, outs, ens = _time_form(usr, torch, w, x, CHOSEN, args.steps, args.warmup,
+                                                               flush, stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     if ws > 1:
@@ -443,7 +456,7 @@ def run_gpu(args):
     # the plain FP32 comparators, same workload and protocol
     comps = {}
     for form in COMPARATORS:
-        tms, _, cc, co, _ = _time_form(usr, torch, w, x, form, args.steps, args.warmup, flush, stream)
+        tms, _, _, cc, co, _ = _time_form(usr, torch, w, x, form, args.steps, args.warmup, flush, stream)
         comps[form[0]] = {"value": evals / ws / (tms / 1e3), "ms_per_step": tms / args.steps,
                           "out_rc8": co[0].double().cpu().numpy()}
         for c in cc:
@@ -459,11 +472,9 @@ def run_gpu(args):
         return
     # the dominant kernel (the pair kernel) and its roofline: its launch duration is the near stage's CUDA-event
     # time on the evaluation stream (events just before and after its launch), averaged over the timed steps
-    per_stage = [sum(stage_ms[k][s] for k in range(len(SWEEP))) / (len(SWEEP) * args.steps)
-                 for s in range(usr.USR_NSTAGES)]
-    dom = usr.STAGES.index("near")
+    per_stage = [sum(stage_ms[k][s] for k in range(len(SWEEP))) / len(SWEEP) for s in range(usr.USR_NSTAGES)]
     flops = sum(p * NEAR_FLOPS_PER_PAIR for p in pairs)                      # one launch per cutoff
-    t_dom = sum(stage_ms[k][dom] for k in range(len(SWEEP))) / args.steps / 1e3
+    t_dom = sum(near_ms) / args.steps / 1e3
     achieved = flops / t_dom / 1e12
     peak_ok = fp32_peak > 0.0
     peak = fp32_peak if peak_ok else FP32_PEAK_DERIVED_TFLOPS

@@ -362,12 +362,17 @@ usr_status usr_debug_parts(usr_ctx* ctx, float* near_out, float* far_out, void* 
 
 enum { USR_NSTAGES = 7 };  /* bin, near, spread, conv_x, conv_y, conv_z, gather */
 
-/* Record CUDA events between the stages of every usr_eval. */
+/*
+ * Record CUDA events in every usr_eval: on = 1 at every stage boundary, on = 2
+ * only just before and after the pair kernel (the least disturbance of the
+ * evaluation's timing), 0 none.  USR_ERR_ARG for other values.
+ */
 usr_status usr_set_profiling(usr_ctx* ctx, int on);
 
 /*
  * Milliseconds of each stage of the last profiled usr_eval (synchronises).
- * ms must hold USR_NSTAGES floats.  The far chain (spread, conv_x/y/z, and the
+ * ms must hold USR_NSTAGES floats; with profiling level 2 only the near stage
+ * (index 1) is measured and the others read 0.  The far chain (spread, conv_x/y/z, and the
  * psi mean, counted in gather) runs on the context's own high-priority stream,
  * concurrently with the near stage on the caller's stream, so the stages can
  * add up to more than the evaluation's duration.

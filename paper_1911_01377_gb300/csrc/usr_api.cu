@@ -95,8 +95,8 @@ struct usr_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // profiling: stage boundary events (see usr_stage_times)
-    bool prof = false;
-    bool prof_valid = false;
+    int prof = 0;                  // 1: events at every stage boundary, 2: around the pair kernel only
+    int prof_valid = 0;
     cudaEvent_t ev[kProfEvents];
     bool ev_made = false;
     cudaStream_t last_stream = nullptr;
@@ -688,7 +688,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     // may start (the far chain joined), 10 end; on the side stream 3 start, 4 spread done, 5-7 passes
     // x, y, z done, 8 psi mean done
     auto mark = [&](int k, cudaStream_t s) {
-        if (c->prof) cudaEventRecord(c->ev[k], s);
+        if (c->prof == 1 || (c->prof == 2 && (k == 1 || k == 2))) cudaEventRecord(c->ev[k], s);
     };
     NvtxRange r_eval("usr_eval");
     mark(0, st);
@@ -990,7 +990,8 @@ extern "C" usr_status usr_debug_parts(usr_ctx* c, float* near_out, float* far_ou
 extern "C" usr_status usr_set_profiling(usr_ctx* c, int on)
 {
     if (!c) return USR_ERR_ARG;
-    c->prof = on != 0;
+    if (on < 0 || on > 2) return USR_ERR_ARG;
+    c->prof = on;
     return USR_OK;
 }
 
@@ -998,6 +999,12 @@ extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
 {
     if (!c || !ms) return USR_ERR_ARG;
     if (!c->prof_valid) return USR_ERR_ARG;
+    if (c->prof_valid == 2) {
+        // the pair kernel alone; the other stages read 0
+        if (cudaEventSynchronize(c->ev[2]) != cudaSuccess) return USR_ERR_CUDA;
+        for (int k = 0; k < USR_NSTAGES; ++k) ms[k] = 0.f;
+        return cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]) == cudaSuccess ? USR_OK : USR_ERR_CUDA;
+    }
     if (cudaEventSynchronize(c->ev[10]) != cudaSuccess) return USR_ERR_CUDA;
     // (from, to) event pairs of the stages; the gather stage adds the psi mean (8 - 7) to the gather itself
     // (10 - 9); the wait for the later of the two branches (between 2 or 8 and 9) is in no stage

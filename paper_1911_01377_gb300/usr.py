@@ -237,8 +237,9 @@ def usr_fp32_peak() -> float:
     return float(v.value)
 
 
-def usr_set_profiling(ctx, on: bool):
-    _check(lib().usr_set_profiling(ctx, int(bool(on))), "usr_set_profiling")
+def usr_set_profiling(ctx, on):
+    """on: True or 1 every stage boundary, 2 the pair kernel only, False or 0 none."""
+    _check(lib().usr_set_profiling(ctx, int(on)), "usr_set_profiling")
 
 
 def usr_stage_times(ctx) -> Tuple[float, ...]:
