@@ -226,9 +226,10 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWE
     so its launch duration is measured inside the timed region); then `stage_steps` more sweeps with every
     stage boundary recorded, outside the timed region, for the stage breakdown.  Returns (total ms, per-stage
     ms means, pair-kernel ms sums of the timed steps, contexts, outs, ens)."""
-    name, conv, P, ratio = form
+    name, conv, P, ratio = form[:4]
+    extra = form[4] if len(form) > 4 else {}
     ctxs = [usr.USeries(w.box, w.grid, r_c, "C1_B2", max_atoms=w.n, conv=conv, spread_points=P,
-                        spread_sigma_over_h=ratio) for r_c in cutoffs]
+                        spread_sigma_over_h=ratio, **extra) for r_c in cutoffs]
     outs = [torch.empty((w.n, 4), dtype=torch.float32, device=x.device) for _ in cutoffs]
     ens = [torch.empty(4, dtype=torch.float64, device=x.device) for _ in cutoffs]
 
@@ -273,7 +274,8 @@ def _time_form(usr, torch, w, x, form, steps, warmup, flush, stream, cutoffs=SWE
     return total, stage, near, ctxs, outs, ens
 
 
-SCALE_FORMS = (CHOSEN, ("tf32x3_gse8", 1, 8, 0.83), COMPARATORS[0], COMPARATORS[1])
+SCALE_FORMS = (CHOSEN, ("bf16x3_gse8_multilevel", 2, 8, 0.83, {"multilevel": 1}), ("tf32x3_gse8", 1, 8, 0.83),
+               COMPARATORS[0], COMPARATORS[1])
 
 
 def run_scale(usr, torch, steps, warmup, flush, stream):
@@ -297,7 +299,7 @@ def run_scale(usr, torch, steps, warmup, flush, stream):
 def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_frac=0.7):
     """Serving form: a stream of `count` independent water boxes (charges log-uniform in
     [2,000, 200,000], 0.1 per A^3, r_c = 9 A, ~1 A grids) through the continuous-batching
-    server (chosen form), first all at once (capacity), then with Poisson arrivals at
+    server (the serving form: TF32x3, 10-point spreading), first all at once (capacity), then with Poisson arrivals at
     rate_frac x capacity (latency); and one system at a time with the plain FP32 form."""
     import numpy as np
     from paper_1911_01377_gb300 import workloads as W
@@ -306,9 +308,8 @@ def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_fra
     xs = [torch.from_numpy(s[3]).pin_memory() for s in systems]
     outs = [torch.empty((s[3].shape[0], 4), dtype=torch.float32).pin_memory() for s in systems]
     ens = [torch.empty(4, dtype=torch.float64).pin_memory() for _ in systems]
-    _, conv, P, ratio = CHOSEN
-    params = [usr.make_params(b, g, rc, "C1_B2", conv=conv, spread_points=P, spread_sigma_over_h=ratio,
-                              max_atoms=x.shape[0]) for (b, g, rc, x) in systems]
+    form = W.SERVING_FORM
+    params = [usr.make_params(b, g, rc, "C1_B2", max_atoms=x.shape[0], **form) for (b, g, rc, x) in systems]
 
     def serve(arrivals):
         srv = usr.Server(hbm_budget_bytes=budget_gib * (1 << 30), slots=slots)
@@ -358,9 +359,9 @@ def run_serving(usr, torch, count, seed=1911, slots=8, budget_gib=64.0, rate_fra
         return t
 
     t_one = one_at_a_time()
-    t_same = one_at_a_time(conv=conv, spread_points=P, spread_sigma_over_h=ratio)
+    t_same = one_at_a_time(**form)
     return {"systems": len(systems), "charges": n_atoms, "slots": slots, "hbm_budget_gib": budget_gib,
-            "form": CHOSEN[0],
+            "form": "tf32x3_gse{spread_points}_w{spread_sigma_over_h:g}".format(**form),
             "capacity_atom_evals_per_s": capacity, "all_at_once_wall_s": wall,
             "poisson_rate_per_s": rate, "poisson_wall_s": wall_p,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),

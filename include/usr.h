@@ -102,6 +102,12 @@ typedef struct {
     int max_atoms;               /* capacity of the context (rows per evaluation) */
     int virial;                  /* 1: also compute the virial tensor (usr_virial); six more far-part
                                     convolution sets per evaluation */
+    int multilevel;              /* 1: the wide Gaussian terms on a grid twice as coarse (Sec. V's remark
+                                    that wider terms can be handled by multilevel summation): the terms
+                                    whose deconvolved width is at least 2.25 coarse spacings on every axis
+                                    are convolved on the coarse grid, reached from the fine grid and back
+                                    by Gaussian restriction and prolongation; needs even grid sizes and
+                                    virial = 0.  0: every term on the fine grid */
 } usr_params;
 
 /* Quantities derived from usr_params (all host-side, FP64). */
@@ -111,13 +117,14 @@ typedef struct {
     double spread_sigma;   /* sigma_s of the spreading Gaussian */
     double h[3];           /* grid spacings L / grid */
     double trunc_bound;    /* Eq. 33 bound for the chosen n_terms */
-    int n_terms;           /* Gaussians on the far grid */
+    int n_terms;           /* Gaussians of the far part (fine and coarse grids together) */
     int cells[3];          /* cell-list cells per axis, floor(L / r_c) */
     int poly_degree;       /* degree of the FP32 polynomial for the wide terms of F */
     int n_explicit;        /* leading Gaussians of F evaluated explicitly in the pair kernel */
     double poly_max_err;   /* max |error| of that polynomial on [0, r_c], relative to F(0) */
     double device_bytes;   /* usr_plan: device memory a new context for these parameters needs;
                               usr_info: device memory the context holds (its buffers only grow) */
+    int n_terms_coarse;    /* of n_terms, those convolved on the coarse grid (multilevel = 1), else 0 */
 } usr_plan_info;
 
 /* Fill *out with a preset row (n_terms = 0, trunc_eps = 0).  Host only. */

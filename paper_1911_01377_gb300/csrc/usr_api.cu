@@ -75,6 +75,14 @@ struct usr_ctx {
     float *d_psiv = nullptr, *d_rho32 = nullptr;
     double *d_vnear = nullptr, *d_vdot = nullptr, *d_vpart = nullptr, *d_W = nullptr;
     bool vir_valid = false;
+    // multilevel: the coarse grid's transfers, its FP32 tables (Bx, Ay, Az, wx, wy, wz) and their input, and
+    // the scratch of the coarse steps (two transfer buffers, coarse rho, X, Y and psi)
+    usr::MlArgs ml{};
+    int mlN = 0;
+    size_t ml_t1 = 0, ml_t2 = 0;
+    double* d_cktab = nullptr;
+    float* d_ctab[6] = {};
+    float* d_mlbuf = nullptr;
     usr::ConvTcMaps maps[3];
     usr::ConvTcArgs targs[3];
     int tbatches[3] = {0, 0, 0};
@@ -130,7 +138,10 @@ void free_all(usr_ctx* c)
                     c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    void* vptrs[] = {c->d_vktab, c->d_psiv, c->d_rho32, c->d_vnear, c->d_vdot, c->d_vpart, c->d_W};
+    void* vptrs[] = {c->d_vktab, c->d_psiv, c->d_rho32, c->d_vnear, c->d_vdot, c->d_vpart, c->d_W,
+                     c->d_cktab, c->d_mlbuf};
+    for (float* p : c->d_ctab)
+        if (p) cudaFree(p);
     for (void* p : vptrs)
         if (p) cudaFree(p);
     for (auto& comp : c->d_vtab)
@@ -252,6 +263,14 @@ double usr::plan_device_bytes(const Plan& P)
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
         b += 8 * G + 48 * near_units((int)ngr) + 8 * (16 + kGridMeanBlocks);
         if (tc) b += 4 * G * (1 + 2 * N);
+    }
+    if (P.Nc > 0) {   // multilevel: weights, coarse tables and their input, scratch, FP32 rho copy (tensor cores)
+        const double Nc = P.Nc, cx = P.nc[0], cy = P.nc[1], cz = P.nc[2], Gc = cx * cy * cz;
+        const double cmax = std::max(cx, std::max(cy, cz));
+        b += 8 * (3 * Nc * cmax + 4 * Nc);
+        b += 4 * Nc * (cx * cx + cy * cy + cz * cz + cx + cy + cz);
+        b += 4 * (std::max(nz * ny * cx, cz * cy * nx) + std::max(nz * cy * cx, cz * ny * nx) + Gc * (2 + 2 * Nc));
+        if (tc && !P.p.virial) b += 4 * G;
     }
     if (!tc) {
         b += 4 * G * (1 + 2 * N) + 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz);
@@ -405,6 +424,48 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
         }
         up.add(c->d_vktab, kt.data(), kt.size());
     }
+    // multilevel: transfer weights (FP32, three axes) and the coarse grid's 1D kernels, in the fine layout
+    usr::ConvTableArgs ctab{};
+    c->mlN = P.Nc;
+    if (P.Nc > 0) {
+        const size_t Nc = (size_t)P.Nc;
+        const int cx = P.nc[0], cy = P.nc[1], cz = P.nc[2];
+        const size_t Gc = (size_t)cx * cy * cz;
+        const int cmax = std::max(cx, std::max(cy, cz));
+        for (int a = 0; a < 3; ++a) {
+            c->ml.n[a] = P.n[a];
+            c->ml.nc[a] = P.nc[a];
+            for (int t = 0; t <= 2 * usr::kMlT; ++t) c->ml.taps.w[a][t] = (float)P.ml_w[a][t];
+        }
+        const size_t nkc = 3 * Nc * (size_t)cmax + 3 * Nc + Nc;
+        ENSURE(c->d_cktab, db * nkc);
+        std::vector<double> kt(nkc, 0.0);
+        for (int a = 0; a < 3; ++a)
+            for (size_t j = 0; j < Nc; ++j) {
+                std::copy(P.ktil_c[a][j].begin(), P.ktil_c[a][j].end(), kt.begin() + (a * Nc + j) * cmax);
+                kt[3 * Nc * cmax + a * Nc + j] = P.mu_c[a][j];
+            }
+        for (size_t j = 0; j < Nc; ++j) kt[3 * Nc * cmax + 3 * Nc + j] = P.scale_c[j];
+        up.add(c->d_cktab, kt.data(), kt.size());
+        ENSURE(c->d_ctab[0], fl * cx * Nc * cx);
+        ENSURE(c->d_ctab[1], fl * Nc * cy * cy);
+        ENSURE(c->d_ctab[2], fl * cz * Nc * cz);
+        ENSURE(c->d_ctab[3], fl * Nc * cx);
+        ENSURE(c->d_ctab[4], fl * Nc * cy);
+        ENSURE(c->d_ctab[5], fl * Nc * cz);
+        c->ml_t1 = std::max((size_t)nz * ny * cx, (size_t)cz * cy * nx);
+        c->ml_t2 = std::max((size_t)nz * cy * cx, (size_t)cz * ny * nx);
+        ENSURE(c->d_mlbuf, fl * (c->ml_t1 + c->ml_t2 + Gc * (2 + 2 * Nc)));
+        if (c->tc) ENSURE(c->d_rho32, fl * G);
+        ctab.N = (int)Nc;
+        ctab.n[0] = cx;
+        ctab.n[1] = cy;
+        ctab.n[2] = cz;
+        ctab.nmax = cmax;
+        ctab.ktil = c->d_cktab;
+        ctab.mu = c->d_cktab + 3 * Nc * cmax;
+        ctab.scale = c->d_cktab + 3 * Nc * cmax + 3 * Nc;
+    }
     usr::ConvTableArgs tab{};
     tab.N = (int)N;
     tab.n[0] = nx;
@@ -524,6 +585,9 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
         for (int cmp = 0; cmp < 6; ++cmp)
             usr::launch_fp32_tables(vtab[cmp], c->d_vtab[cmp][0], c->d_vtab[cmp][1], c->d_vtab[cmp][2],
                                     c->d_vtab[cmp][3], c->d_vtab[cmp][4], c->d_vtab[cmp][5], st);
+    if (c->mlN > 0)
+        usr::launch_fp32_tables(ctab, c->d_ctab[0], c->d_ctab[1], c->d_ctab[2], c->d_ctab[3], c->d_ctab[4],
+                                c->d_ctab[5], st);
     return check_launch();
 }
 
@@ -627,18 +691,22 @@ usr::ClusterList cluster_list(const usr_ctx* c)
  * {Bx, Ay, Az, wx, wy, wz} into psi (X and Y are the context's scratch); after
  * each pass `after(k)` is called (stage marks).
  */
+struct Conv3 {
+    int N, nx, ny, nz;
+    float *X, *Y;     // scratch of N * nx * ny * nz floats each
+};
+
 template <typename F>
-void fp32_conv(usr_ctx* c, const float* rho, float* const* t, float* psi, cudaStream_t st, F after)
+void conv3(const Conv3& d, const float* rho, float* const* t, float* psi, cudaStream_t st, F after)
 {
-    const Plan& P = c->plan;
-    const int N = P.N, nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const long long G = c->G;
+    const int N = d.N, nx = d.nx, ny = d.ny, nz = d.nz;
+    const long long G = (long long)nx * ny * nz;
     {   // x pass: all terms
         usr::ConvGemm g{};
         g.M = ny * nz; g.N = N * nx; g.K = nx;
         g.A = rho; g.lda = nx;
         g.B = t[0]; g.ldb = (long long)N * nx;
-        g.C = c->d_X; g.ldc = nx;
+        g.C = d.X; g.ldc = nx;
         g.nb2 = 1; g.nsplit = nx; g.c_split = G;
         g.mode = 1; g.dcw = t[3]; g.mean = nullptr;   // rho has its mean removed already
         usr::launch_conv(g, 1, st);
@@ -648,8 +716,8 @@ void fp32_conv(usr_ctx* c, const float* rho, float* const* t, float* psi, cudaSt
         usr::ConvGemm g{};
         g.M = ny; g.N = nx; g.K = ny;
         g.A = t[1]; g.lda = ny; g.a_s1 = (long long)ny * ny; g.a_s2 = 0;
-        g.B = c->d_X; g.ldb = nx; g.b_s1 = G; g.b_s2 = (long long)ny * nx;
-        g.C = c->d_Y; g.ldc = nx; g.c_s1 = G; g.c_s2 = (long long)ny * nx;
+        g.B = d.X; g.ldb = nx; g.b_s1 = G; g.b_s2 = (long long)ny * nx;
+        g.C = d.Y; g.ldc = nx; g.c_s1 = G; g.c_s2 = (long long)ny * nx;
         g.nb2 = nz; g.nsplit = 1 << 30; g.c_split = 0;
         g.mode = 2; g.dcw = t[4]; g.dcw_s1 = ny;
         usr::launch_conv(g, N * nz, st);
@@ -659,13 +727,20 @@ void fp32_conv(usr_ctx* c, const float* rho, float* const* t, float* psi, cudaSt
         usr::ConvGemm g{};
         g.M = nz; g.N = nx * ny; g.K = N * nz;
         g.A = t[2]; g.lda = (long long)N * nz;
-        g.B = c->d_Y; g.ldb = (long long)nx * ny;
+        g.B = d.Y; g.ldb = (long long)nx * ny;
         g.C = psi; g.ldc = (long long)nx * ny;
         g.nb2 = 1; g.nsplit = 1 << 30; g.c_split = 0;
         g.mode = 2; g.dcw = t[5]; g.dcw_s1 = 0;
         usr::launch_conv(g, 1, st);
     }
     after(2);
+}
+
+template <typename F>
+void fp32_conv(usr_ctx* c, const float* rho, float* const* t, float* psi, cudaStream_t st, F after)
+{
+    const Plan& P = c->plan;
+    conv3(Conv3{P.N, P.n[0], P.n[1], P.n[2], c->d_X, c->d_Y}, rho, t, psi, st, after);
 }
 
 /* The evaluation sequence; xyzq/out are device pointers already checked. */
@@ -712,7 +787,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         if (c->tc)
             usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
                                c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status,
-                               sd, c->vir ? c->d_rho32 : nullptr);
+                               sd, (c->vir || c->mlN > 0) ? c->d_rho32 : nullptr);
         else
             usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
                                c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd);
@@ -728,6 +803,20 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         } else {
             float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
             fp32_conv(c, c->d_rho, t, c->d_psi, sd, [&](int k) { mark(5 + k, sd); });
+        }
+        if (c->mlN > 0) {
+            // the wide terms on the coarse grid, added to psi (Sec. V, multilevel)
+            const Plan& Q = c->plan;
+            const size_t Gc = (size_t)Q.nc[0] * Q.nc[1] * Q.nc[2];
+            float* t1 = c->d_mlbuf;
+            float* t2 = t1 + c->ml_t1;
+            float* rc = t2 + c->ml_t2;
+            float* Xc = rc + Gc;
+            float* Yc = Xc + (size_t)c->mlN * Gc;
+            float* pc = Yc + (size_t)c->mlN * Gc;
+            usr::launch_ml_restrict(c->ml, c->tc ? c->d_rho32 : c->d_rho, t1, t2, rc, nullptr, c->d_status, sd);
+            conv3(Conv3{c->mlN, Q.nc[0], Q.nc[1], Q.nc[2], Xc, Yc}, rc, c->d_ctab, pc, sd, [](int) {});
+            usr::launch_ml_prolong(c->ml, pc, t1, t2, c->d_psi, c->d_status, sd);
         }
         usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
         mark(8, sd);

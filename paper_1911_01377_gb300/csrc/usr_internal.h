@@ -18,6 +18,7 @@ namespace usr {
 constexpr int kMaxPolyDeg = 24;
 constexpr int kMaxExplicit = 8;
 constexpr int kMaxTerms = 16;
+constexpr int kMlT = 16;           // multilevel transfer half-width in fine points: ceil(6 x 2.6)
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 
@@ -55,7 +56,7 @@ struct Plan {
     double sigma_sa[3];                  // spreading width per axis
     double wsum;                         // sum of the spreading weights over a stencil
     int P;                               // stencil points per axis
-    int N;                               // far-grid Gaussians
+    int N;                               // far Gaussians on the fine grid (all of them unless multilevel)
     std::vector<double> a, s;            // full real-space term table (a_j, s_j)
     // pair kernel: F(u = r^2) = sum_{e < n_explicit} ea_e exp(-u * einv_e) + poly(2u/r_c^2 - 1)
     int n_explicit;
@@ -71,6 +72,16 @@ struct Plan {
     // virial: first and second derivatives (in x) of the same periodised kernels, split the same way
     std::vector<double> ktil_d[2][3][kMaxTerms];
     double mu_d[2][3][kMaxTerms];
+    // multilevel (usr_params.multilevel): terms N .. N + Nc - 1 on the coarse grid nc = n / 2 (spacing 2 h).
+    // Per axis, restriction r(G) = sum_g eR(g - 2G) f(g) and prolongation f(g) = sum_G eP(g - 2G) t(G) with
+    // the banded periodised Gaussian weights ml_w[a][t + kMlT], t = -kMlT .. kMlT (the same width both
+    // ways); the coarse 1D kernels ktil_c / mu_c and scale_c as for the fine grid.
+    int Nc = 0;
+    int nc[3];
+    std::vector<double> ml_w[3];
+    std::vector<double> ktil_c[3][kMaxTerms];
+    double mu_c[3][kMaxTerms];
+    double scale_c[kMaxTerms];
     int cells[3];
     TileGeom tile;
     std::vector<int> tile_org[3];        // per axis: tile origin of each block
@@ -211,7 +222,24 @@ struct ConvTcMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
+/* Grid transfers of the multilevel far part (k_multilevel.cu): fine n, coarse nc = n / 2 per axis, banded
+   weights w[a][t + kMlT] for t = -kMlT .. kMlT (passed by value: constant-bank operands). */
+struct MlTaps {
+    float w[3][2 * kMlT + 1];
+};
+struct MlArgs {
+    int n[3], nc[3];
+    MlTaps taps;
+};
+
 // ---- launchers (all enqueue on `st`) ----
+/* rho (fine, [z][y][x]) -> rho_c (coarse) through t1 = [n2][n1][nc0], t2 = [n2][nc1][nc0]; with rho_c_lo
+   non-null, rho_c / rho_c_lo receive the TF32 hi / lo split of the result (tensor-core coarse passes). */
+void launch_ml_restrict(const MlArgs& m, const float* rho, float* t1, float* t2, float* rho_c, float* rho_c_lo,
+                        int* status, cudaStream_t st);
+/* psi += prolongation of psi_c, through t1 = [nc2][nc1][n0], t2 = [nc2][n1][n0] */
+void launch_ml_prolong(const MlArgs& m, const float* psi_c, float* t1, float* t2, float* psi, int* status,
+                       cudaStream_t st);
 cudaError_t launch_bin(int n, const float4* xyzq, const BoxF& b, int ncell, int* count, int* cell_of, int* slot,
                        float4* wpos, int* cell_start, int* pstart, int* unsorted, int* perm, float4* spos,
                        int* status, cudaStream_t st);

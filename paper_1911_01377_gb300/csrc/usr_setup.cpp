@@ -265,7 +265,8 @@ usr_status make_plan(const usr_params* pp, Plan* out)
         for (int a = 0; a < 3; ++a)
             if (p.grid[a] % q != 0) return USR_ERR_BOX;
     }
-    if (p.max_atoms < 0 || (p.virial != 0 && p.virial != 1)) return USR_ERR_ARG;
+    if (p.max_atoms < 0 || (p.virial != 0 && p.virial != 1) || (p.multilevel != 0 && p.multilevel != 1))
+        return USR_ERR_ARG;
     int Pst = p.spread_points ? p.spread_points : 12;
     if (Pst < 8 || Pst > 16 || (Pst & 1)) return USR_ERR_ARG;
     double ratio = p.spread_sigma_over_h > 0.0 ? p.spread_sigma_over_h : 1.0;
@@ -326,6 +327,58 @@ usr_status make_plan(const usr_params* pp, Plan* out)
                     P.mu_d[o][a][j] = periodic_kernel_deriv(wc, P.h[a], P.n[a], o + 1, P.ktil_d[o][a][j]);
         }
         P.scale[j] = f;
+    }
+    // multilevel: the wide terms on a grid twice as coarse.  Per axis, with H = 2 h and widths a = b of the
+    // restriction and prolongation Gaussians and c of the coarse kernel (w^2 = a^2 + b^2 + c^2),
+    //   e_w = w / (2 pi a b c) (e_b * e_c * e_a),
+    // and the two outer convolution integrals become sums over the coarse grid (a factor H each); the sums
+    // approximate the integrals to about exp(-2 pi^2 v^2 / H^2) with v the width of the integrand's
+    // narrowest Gaussian factor, so a = b = 1.3 H and c >= 1.3 H keep that near 1e-7.  A term goes to the
+    // coarse grid from the first j whose deconvolved width is at least 2.25 H on every axis (the widths
+    // grow with j); term 0 stays on the fine grid.
+    if (p.multilevel) {
+        if (p.virial) return USR_ERR_BOX;
+        double ma[3];
+        for (int a = 0; a < 3; ++a) {
+            if (P.n[a] % 2 != 0 || P.n[a] / 2 < 8) return USR_ERR_BOX;
+            P.nc[a] = P.n[a] / 2;
+            const double H = 2.0 * P.h[a];
+            ma[a] = 1.3 * H;
+            const int T = kMlT;   // six widths a = 2.6 h: 15.6 points
+            if (2 * T + 1 > P.n[a]) return USR_ERR_BOX;
+            P.ml_w[a].assign(2 * T + 1, 0.0);
+            for (int t = -T; t <= T; ++t) {
+                double v = 0.0;
+                for (int im = -1; im <= 1; ++im) {
+                    const double x = (t + im * P.n[a]) * P.h[a];
+                    v += std::exp(-x * x / (2.0 * ma[a] * ma[a]));
+                }
+                P.ml_w[a][t + T] = v;
+            }
+        }
+        int jw = P.N;
+        for (int j = 1; j < P.N && jw == P.N; ++j) {
+            bool wide = true;
+            for (int a = 0; a < 3; ++a) {
+                const double w = std::sqrt(P.s[j] * P.s[j] - 2.0 * P.sigma_sa[a] * P.sigma_sa[a]);
+                if (w < 2.25 * 2.0 * P.h[a]) wide = false;
+            }
+            if (wide) jw = j;
+        }
+        P.Nc = P.N - jw;
+        for (int jj = 0; jj < P.Nc; ++jj) {
+            const int j = jw + jj;
+            double f = P.scale[j];
+            for (int a = 0; a < 3; ++a) {
+                const double H = 2.0 * P.h[a];
+                const double w = std::sqrt(P.s[j] * P.s[j] - 2.0 * P.sigma_sa[a] * P.sigma_sa[a]);
+                const double c = std::sqrt(w * w - 2.0 * ma[a] * ma[a]);
+                f *= w / (2.0 * kPi * ma[a] * ma[a] * c) * H * H;
+                P.mu_c[a][jj] = periodic_kernel(c, H, P.nc[a], P.ktil_c[a][jj]);
+            }
+            P.scale_c[jj] = f;
+        }
+        P.N = jw;
     }
     // sum of the spreading weights over a stencil: prod_a sqrt(2 pi) sigma_a / h_a
     P.wsum = std::pow(2.0 * kPi, 1.5) * ratio * ratio * ratio;
@@ -424,8 +477,9 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     I.F0 = P.F0;
     I.spread_sigma = P.sigma_s;
     for (int a = 0; a < 3; ++a) { I.h[a] = P.h[a]; I.cells[a] = P.cells[a]; }
-    I.trunc_bound = trunc_bound(P.N, se.b, P.sigma, Lmax);
-    I.n_terms = P.N;
+    I.trunc_bound = trunc_bound(P.N + P.Nc, se.b, P.sigma, Lmax);
+    I.n_terms = P.N + P.Nc;
+    I.n_terms_coarse = P.Nc;
     I.poly_degree = P.poly_deg;
     I.n_explicit = P.n_explicit;
     I.poly_max_err = ev;

@@ -32,13 +32,13 @@ class usr_series(ctypes.Structure):
 class usr_params(ctypes.Structure):
     _fields_ = [("box", _c_d * 3), ("grid", _c_i * 3), ("r_c", _c_d), ("series", usr_series),
                 ("spread_sigma_over_h", _c_d), ("spread_points", _c_i), ("conv", _c_i), ("max_atoms", _c_i),
-                ("virial", _c_i)]
+                ("virial", _c_i), ("multilevel", _c_i)]
 
 
 class usr_plan_info(ctypes.Structure):
     _fields_ = [("sigma", _c_d), ("F0", _c_d), ("spread_sigma", _c_d), ("h", _c_d * 3), ("trunc_bound", _c_d),
                 ("n_terms", _c_i), ("cells", _c_i * 3), ("poly_degree", _c_i), ("n_explicit", _c_i),
-                ("poly_max_err", _c_d), ("device_bytes", _c_d)]
+                ("poly_max_err", _c_d), ("device_bytes", _c_d), ("n_terms_coarse", _c_i)]
 
 
 class usr_server_params(ctypes.Structure):
@@ -127,7 +127,7 @@ def usr_series_preset(preset) -> usr_series:
 
 
 def make_params(box, grid, r_c, series, spread_sigma_over_h=0.0, spread_points=0, conv=0, max_atoms=0,
-                n_terms=0, trunc_eps=0.0, virial=0) -> usr_params:
+                n_terms=0, trunc_eps=0.0, virial=0, multilevel=0) -> usr_params:
     if isinstance(series, (str, int)):
         series = usr_series_preset(series)
     elif not isinstance(series, usr_series):
@@ -145,6 +145,7 @@ def make_params(box, grid, r_c, series, spread_sigma_over_h=0.0, spread_points=0
     p.conv = int(conv)
     p.max_atoms = int(max_atoms)
     p.virial = int(virial)
+    p.multilevel = int(multilevel)
     return p
 
 

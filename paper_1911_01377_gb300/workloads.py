@@ -365,6 +365,13 @@ def lattice_water_box(seed: int, n_charges: int, density: float = 0.1) -> Tuple[
     return (L, L, L), np.ascontiguousarray(rows.astype(np.float32))
 
 
+# The serving stream's evaluation form: TF32x3 tensor-core convolutions and a 10-point spreading stencil of
+# width 0.9 h.  On its ~1 A grids at r_c = 9 A the 8-point stencil (width 0.83 h) leaves about 1.2e-4 of the
+# far potential, and single-grid BF16x3 about 6e-4 (the wide terms' near-constant parts carry the operand
+# rounding of the 16-bit split); this form stays near 2e-5.
+SERVING_FORM = dict(conv=1, spread_points=10, spread_sigma_over_h=0.9)
+
+
 def serving_stream(seed: int, count: int, n_min: int = 2000, n_max: int = 200000, density: float = 0.1,
                    spacing: float = 1.0, r_c: float = 9.0, grid_multiple: int = 8):
     """The serving workload: `count` independent water boxes with charge counts

@@ -110,3 +110,23 @@ def test_static_cell_list_refuses_oversized_cell_counts(libusr):
     with pytest.raises(usr.UsrError) as e:          # mean occupancy above 2,048 atoms per cell
         usr.usr_cells_static(2049 * 27, None, (10.0, 10.0, 10.0), (3, 3, 3), None, None, None, None, 0)
     assert e.value.code == 7
+
+
+def test_multilevel_plan(libusr):
+    """The multilevel option moves the wide terms to the coarse grid (the threshold is on the deconvolved
+    width: at least 2.25 coarse spacings on every axis); it needs even grid sizes and no virial."""
+    box, grid = (220.0,) * 3, (176,) * 3
+    plain = usr.usr_plan(usr.make_params(box, grid, 10.0, "C1_B2", max_atoms=10, conv=2))
+    ml = usr.usr_plan(usr.make_params(box, grid, 10.0, "C1_B2", max_atoms=10, conv=2, multilevel=1))
+    assert plain.n_terms_coarse == 0
+    assert ml.n_terms == plain.n_terms and 0 < ml.n_terms_coarse < ml.n_terms
+    assert ml.trunc_bound == plain.trunc_bound
+    for kw in [dict(grid=(176, 176, 175)), dict(virial=1)]:
+        args = dict(box=box, grid=grid, r_c=10.0, series="C1_B2", max_atoms=10, multilevel=1)
+        args.update(kw)
+        with pytest.raises(usr.UsrError) as e:
+            usr.usr_plan(usr.make_params(**args))
+        assert e.value.code == 2
+    with pytest.raises(usr.UsrError) as e:
+        usr.usr_plan(usr.make_params(box, grid, 10.0, "C1_B2", max_atoms=10, multilevel=2))
+    assert e.value.code == 1

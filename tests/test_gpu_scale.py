@@ -1,7 +1,8 @@
 """Precision forms at scale: 354,933 rigid waters (1,064,799 charges) in a
 cubic box L = 220 A at 0.1 charges/A^3, r_c = 10 A, 176^3 grid, evaluated by
-the FP32 path and by the two tensor-core convolution forms (TF32x3, BF16x3;
-FP32 accumulation, hi/lo split operands, energies reduced in FP64).
+the FP32 path, by the two tensor-core convolution forms (TF32x3, BF16x3;
+FP32 accumulation, hi/lo split operands, energies reduced in FP64), and by
+BF16x3 with the wide terms on a coarse grid (multilevel).
 
 The FP64 oracle cannot give every atom's near sum at this size in test time,
 so the checks are on outputs it can compute one by one and on identities that
@@ -37,6 +38,7 @@ N_TARGETS = 10000
 TOL = {0: dict(far_phi=2e-5, far_F=1e-4, phi=1e-5, F=1e-5, E_far=2e-5),
        1: dict(far_phi=2e-5, far_F=1e-4, phi=1e-5, F=1e-5, E_far=2e-5),
        2: dict(far_phi=1e-4, far_F=1e-3, phi=1e-4, F=1e-4, E_far=1e-4)}
+TOL["ml2"] = TOL[2]
 TOL_NEAR = 2e-6
 
 
@@ -57,8 +59,10 @@ def scale():
     ref = O.evaluate(ser, R_C, w.box, pos, q, targets=targets, kmax=6.5 / float(np.min(s)))
     gpu = {}
     x = torch.from_numpy(w.xyzq).cuda()
-    for conv in (0, 1, 2):
-        ctx = usr.USeries(w.box, w.grid, R_C, "C1_B2", max_atoms=w.n, conv=conv)
+    for conv in (0, 1, 2, "ml2"):
+        # "ml2": BF16x3 with the wide terms on the coarse grid (multilevel)
+        kw = dict(conv=2, multilevel=1) if conv == "ml2" else dict(conv=conv)
+        ctx = usr.USeries(w.box, w.grid, R_C, "C1_B2", max_atoms=w.n, **kw)
         usr.usr_set_keep_parts(ctx.ctx, True)
         out, en = ctx.eval(x)
         near, far = ctx.parts(w.n)
@@ -75,11 +79,11 @@ def test_near_at_targets(scale):
     g = gpu[0]
     assert O.rms_rel(g["near"][t, 3], ref.phi_near) < TOL_NEAR
     assert O.rms_rel(g["near"][t, :3], ref.F_near) < TOL_NEAR
-    for conv in (1, 2):                                  # the near part does not depend on the form
+    for conv in (1, 2, "ml2"):                           # the near part does not depend on the form
         assert np.array_equal(gpu[conv]["near"], g["near"])
 
 
-@pytest.mark.parametrize("conv", [0, 1, 2])
+@pytest.mark.parametrize("conv", [0, 1, 2, "ml2"])
 def test_far_and_total_at_targets(scale, conv):
     w, t, q, ref, gpu = scale
     g, tol = gpu[conv], TOL[conv]
@@ -90,7 +94,7 @@ def test_far_and_total_at_targets(scale, conv):
         assert v < tol[k], k
 
 
-@pytest.mark.parametrize("conv", [0, 1, 2])
+@pytest.mark.parametrize("conv", [0, 1, 2, "ml2"])
 def test_energies(scale, conv):
     w, t, q, ref, gpu = scale
     g = gpu[conv]["E"]

@@ -31,12 +31,24 @@ def env():
     return torch, usr, systems
 
 
-def _alone(torch, usr, box, grid, r_c, xyzq, conv):
-    ctx = usr.USeries(box, grid, r_c, "C1_B2", max_atoms=xyzq.shape[0], conv=conv)
+FORMS = {"fp32": dict(conv=0), "serving": W.SERVING_FORM}
+
+
+def _form(conv):
+    return FORMS[conv] if isinstance(conv, str) else dict(conv=conv)
+
+
+def _alone(torch, usr, box, grid, r_c, xyzq, conv, parts=False):
+    ctx = usr.USeries(box, grid, r_c, "C1_B2", max_atoms=xyzq.shape[0], **_form(conv))
+    if parts:
+        usr.usr_set_keep_parts(ctx.ctx, True)
     out, en = ctx.eval(torch.from_numpy(xyzq).cuda())
+    far = ctx.parts(xyzq.shape[0])[1] if parts else None
     torch.cuda.synchronize()
     assert usr.usr_last_device_status(ctx.ctx) == 0
     r = out.cpu().numpy(), en.cpu().numpy()
+    if parts:
+        r = r + (far.cpu().numpy(),)
     ctx.close()
     return r
 
@@ -45,7 +57,7 @@ def _serve(torch, usr, systems, conv, budget=0.0, slots=4):
     srv = usr.Server(hbm_budget_bytes=budget, slots=slots)
     bufs = []
     for box, grid, r_c, xyzq in systems:
-        p = usr.make_params(box, grid, r_c, "C1_B2", conv=conv, max_atoms=xyzq.shape[0])
+        p = usr.make_params(box, grid, r_c, "C1_B2", max_atoms=xyzq.shape[0], **_form(conv))
         x = torch.from_numpy(xyzq).pin_memory()
         o = torch.empty((xyzq.shape[0], 4), dtype=torch.float32).pin_memory()
         e = torch.empty(4, dtype=torch.float64).pin_memory()
@@ -58,7 +70,7 @@ def _serve(torch, usr, systems, conv, budget=0.0, slots=4):
     return bufs, done, held
 
 
-@pytest.mark.parametrize("conv", [0, 2])
+@pytest.mark.parametrize("conv", [0, 2, "serving"])
 def test_same_alone_and_in_the_mix(env, conv):
     torch, usr, systems = env
     bufs, done, _ = _serve(torch, usr, systems, conv)
@@ -99,3 +111,23 @@ def test_served_result_matches_oracle(env):
     ref = O.evaluate(O.Series(*paper_tables()["table2_C1"]), r_c, box, xyzq[:, :3], xyzq[:, 3])
     assert abs(e.numpy()[0] / ref.E - 1.0) < 1e-6
     assert O.rms_rel(o.numpy()[:, :3].astype(np.float64), ref.F) < 1e-5
+
+
+def test_serving_form_against_oracle(env):
+    """The serving stream's form on a system of its largest sizes (100k charges, 96^3 grid of 1.04 A,
+    r_c = 9 A), against the FP64 oracle with the bounds of the tensor-core forms (far potential 1e-4,
+    far force 1e-3, total force 1e-4, energy 1e-6), and the same system through the server bit for bit."""
+    torch, usr, _ = env
+    (box, grid, r_c, xyzq), = W.serving_stream(7, 1, n_min=100000, n_max=100000)
+    out, en, far = _alone(torch, usr, box, grid, r_c, xyzq, "serving", parts=True)
+    from tests.golden import paper_tables
+    ref = O.evaluate(O.Series(*paper_tables()["table2_C1"]), r_c, box, xyzq[:, :3], xyzq[:, 3])
+    far = far.astype(np.float64)
+    assert O.rms_rel(far[:, 3], ref.phi_far) < 1e-4
+    assert O.rms_rel(far[:, :3], ref.F_far) < 1e-3
+    assert O.rms_rel(out[:, :3].astype(np.float64), ref.F) < 1e-4
+    assert abs(en[0] / ref.E - 1.0) < 1e-6
+    bufs, done, _ = _serve(torch, usr, [(box, grid, r_c, xyzq)], "serving")
+    (t, o, e), = bufs
+    assert done[t][1] == 0
+    assert np.array_equal(o.numpy(), out) and np.array_equal(e.numpy(), en)
