@@ -450,23 +450,17 @@ __device__ __forceinline__ float4 near_part(const unsigned long long* __restrict
 template <int P>
 __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict__ pos,
                                                         const int* __restrict__ cell_start,
-                                                        const int* __restrict__ perm,
-                                                        const unsigned long long* __restrict__ near_acc,
                                                         const float* __restrict__ psi, GridArgs g,
-                                                        float4* __restrict__ out, float4* __restrict__ near_dbg,
-                                                        float4* __restrict__ far_dbg, double* __restrict__ partial,
-                                                        unsigned int* __restrict__ counter,
-                                                        double* __restrict__ energy, int* __restrict__ status)
+                                                        float4* __restrict__ far4, double* __restrict__ partial,
+                                                        int* __restrict__ status)
 {
     constexpr int H = P / 2;
-    constexpr int NIT = (P * P + 31) / 32;
     extern __shared__ float4 smem4[];
     float* tile = reinterpret_cast<float*>(smem4);
     __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
-    __shared__ double red[kWarps][4];
-    __shared__ float4 sp[kGChunk], sn[kGChunk];   // staged atoms: position/charge, near part
-    __shared__ int si[kGChunk];                   // and caller index
-    __shared__ int is_last;
+    __shared__ double red[kWarps][2];
+    __shared__ float4 sp[kGChunk];                // staged atoms: position/charge
+    __shared__ int si[kGChunk];                   // and sorted index
     const int Tx = g.tg.T[0], Ty = g.tg.T[1], Tz = g.tg.T[2];
     const int TXY = Tx * Ty;
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
@@ -492,18 +486,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict
     // the stencil columns jx = u, u + 4, ... of every row, contracting z first
     constexpr int NC = (P + 3) / 4;
     const int quad = lane >> 2, u = lane & 3;
-    CSum qn, qf, qq;                                       // sums of q phi_near, q phi_far, q^2
+    CSum qf, qq;                                           // sums of q phi_far, q^2
     const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
     for (int c0 = 0; c0 < natoms; c0 += kGChunk) {
         const int nch = min(kGChunk, natoms - c0);
         __syncthreads();                           // the previous chunk is done
         for (int a = threadIdx.x; a < nch; a += kThreads) {
-            int s = block_atom(c0 + a, rs, pre);
-            if (!USR_IN_BOUNDS(s, g.max_atoms, status)) s = 0;
-            sp[a] = pos[s];
-            sn[a] = near_part(near_acc, s);
-            const int ci = perm[s];
-            si[a] = USR_IN_BOUNDS(ci, g.max_atoms, status) ? ci : -1;
+            const int s = block_atom(c0 + a, rs, pre);
+            const bool in = USR_IN_BOUNDS(s, g.max_atoms, status);
+            sp[a] = pos[in ? s : 0];
+            si[a] = in ? s : -1;
         }
         __syncthreads();
         for (int j0 = warp * 8; j0 < nch; j0 += kWarps * 8) {
@@ -583,65 +575,94 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict
             }
             aphi -= phi_dc;
             if (have && u == 0 && si[j] >= 0) {
-                const int i = si[j];
                 const float qi = p.w;
-                const float4 nr = sn[j];
-                const float fx = -qi * ax, fy = -qi * ay, fz = -qi * az;
-                const float phi = nr.w + aphi - g.F0 * qi;
-                out[i] = make_float4(nr.x + fx, nr.y + fy, nr.z + fz, phi);
-                if (near_dbg) near_dbg[i] = nr;
-                if (far_dbg) far_dbg[i] = make_float4(fx, fy, fz, aphi);
-                qn.add_product(qi, nr.w);
+                far4[si[j]] = make_float4(-qi * ax, -qi * ay, -qi * az, aphi);
                 qf.add_product(qi, aphi);
                 qq.add_product(qi, qi);
             }
         }
     }
-    // per-warp energy sums in a fixed order (lanes 0, 4, ..., 28 hold atoms)
-    double e_near = 0.5 * qn.value(), e_far = 0.5 * qf.value(), e_self = -0.5 * g.F0d * qq.value();
-    double e_tot = e_near + e_far + e_self;
-    e_tot = warp_sum_d(e_tot);
-    e_near = warp_sum_d(e_near);
-    e_far = warp_sum_d(e_far);
-    e_self = warp_sum_d(e_self);
+    // per-warp sums in a fixed order (lanes 0, 4, ..., 28 hold atoms), then per block: E_far, E_self
+    double e_far = warp_sum_d(0.5 * qf.value()), e_self = warp_sum_d(-0.5 * g.F0d * qq.value());
     if (lane == 0) {
-        red[warp][0] = e_tot;
-        red[warp][1] = e_near;
-        red[warp][2] = e_far;
-        red[warp][3] = e_self;
+        red[warp][0] = e_far;
+        red[warp][1] = e_self;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 2) {
         double v = 0.0;
         for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
-        __threadfence();
+        partial[(size_t)blockIdx.x * 2 + threadIdx.x] = v;
     }
+}
+
+/*
+ * After the pair kernel and the far gather: per sorted atom s, the result in caller order,
+ *   out[perm[s]] = (F_near + F_far, phi_near + phi_far - F(0) q),
+ * and the energies E = E_near + E_far + E_self (Eq. 20's near sum, the grid part, the self term), the
+ * E_near sum per block here, the E_far / E_self sums per tile block from the gather, all reduced in a
+ * fixed order by the last block.
+ */
+__global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __restrict__ pos,
+                                                      const int* __restrict__ perm,
+                                                      const unsigned long long* __restrict__ near_acc,
+                                                      const float4* __restrict__ far4, float F0, int nfar,
+                                                      const double* __restrict__ far_partial,
+                                                      float4* __restrict__ out, float4* __restrict__ near_dbg,
+                                                      float4* __restrict__ far_dbg, double* __restrict__ partial,
+                                                      unsigned int* __restrict__ counter,
+                                                      double* __restrict__ energy, int max_atoms,
+                                                      int* __restrict__ status)
+{
+    __shared__ double red[kWarps][3];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    CSum qn;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < n; s += gridDim.x * kThreads) {
+        const float4 nr = near_part(near_acc, s), f = far4[s];
+        const float qi = pos[s].w;
+        const int i = perm[s];
+        if (!USR_IN_BOUNDS(i, max_atoms, status)) continue;
+        out[i] = make_float4(nr.x + f.x, nr.y + f.y, nr.z + f.z, nr.w + f.w - F0 * qi);
+        if (near_dbg) near_dbg[i] = nr;
+        if (far_dbg) far_dbg[i] = f;
+        qn.add_product(qi, nr.w);
+    }
+    const double e_near = warp_sum_d(0.5 * qn.value());
+    if (lane == 0) red[warp][0] = e_near;
     __syncthreads();
     if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += red[w][0];
+        partial[blockIdx.x] = v;
+        __threadfence();
         const unsigned int ticket = atomicAdd(counter, 1u);
         is_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (is_last) {
-        __threadfence();
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) {
-            #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += ((volatile double*)partial)[(size_t)k * 4 + c];
-        }
-        #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = warp_sum_d(acc[c]);
-        __syncthreads();
-        if (lane == 0)
-            for (int c = 0; c < 4; ++c) red[warp][c] = acc[c];
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double v = 0.0;
-            for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-            energy[threadIdx.x] = v;
-        }
-        if (threadIdx.x == 0) *counter = 0u;
+    if (!is_last) return;
+    __threadfence();
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) acc[0] += ((volatile double*)partial)[k];
+    for (int k = threadIdx.x; k < nfar; k += kThreads) {
+        acc[1] += far_partial[(size_t)k * 2];
+        acc[2] += far_partial[(size_t)k * 2 + 1];
+    }
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = warp_sum_d(acc[c]);
+    __syncthreads();
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) red[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e[3] = {0.0, 0.0, 0.0};
+        for (int w = 0; w < kWarps; ++w)
+            for (int c = 0; c < 3; ++c) e[c] += red[w][c];
+        energy[0] = e[0] + e[1] + e[2];
+        energy[1] = e[0];
+        energy[2] = e[1];
+        energy[3] = e[2];
+        *counter = 0u;
     }
 }
 
@@ -698,15 +719,13 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
         k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr, status);
 }
 
-#define USR_GATHER_CASE(PP)                                                                                      \
-    case PP:                                                                                                     \
-        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, perm, near_acc, psi, g, out, near_dbg, far_dbg, \
-                                                  partial, counter, energy, status);                             \
+#define USR_GATHER_CASE(PP)                                                                                  \
+    case PP:                                                                                                 \
+        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, psi, g, far4, partial, status);           \
         break;
 
-void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm, const unsigned long long* near_acc,
-                   const float* psi, const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg,
-                   double* partial, unsigned int* counter, double* energy, int* status, cudaStream_t st)
+void launch_gather(int P, const float4* spos, const int* cell_start, const float* psi, const GridArgs& g,
+                   float4* far4, double* partial, int* status, cudaStream_t st)
 {
     const int nb = tile_blocks(g.tg);
     const size_t smem = sizeof(float) * tile_floats(g.tg);
@@ -718,6 +737,16 @@ void launch_gather(int P, const float4* spos, const int* cell_start, const int* 
         default:
         USR_GATHER_CASE(16)
     }
+}
+
+void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
+                    const float4* far4, float F0, int nfar, const double* far_partial, float4* out,
+                    float4* near_dbg, float4* far_dbg, double* partial, unsigned int* counter, double* energy,
+                    int max_atoms, int* status, cudaStream_t st)
+{
+    const int nb = std::max(1, std::min(kCombineBlocks, (n + kThreads - 1) / kThreads));
+    k_combine<<<nb, kThreads, 0, st>>>(n, spos, perm, near_acc, far4, F0, nfar, far_partial, out, near_dbg, far_dbg,
+                                       partial, counter, energy, max_atoms, status);
 }
 
 }  // namespace usr

@@ -57,25 +57,45 @@ __device__ __forceinline__ long long offs(int col, int g, int b, int d0, int d1,
 }
 
 /*
- * Stage rows [g0, g0 + rows) (periodic in n_in) of 32 columns starting at col0 into S[row][col].  Columns
- * past ncol read as zero.
+ * Stage rows [g0, g0 + ROWS) (periodic in n_in) of 32 columns starting at col0 into S[row][col].  Columns
+ * past ncol read as zero.  All of a thread's loads are issued before its shared-memory stores.
  */
-template <int AX>
-__device__ __forceinline__ void stage(float (*S)[kMlPad], const float* __restrict__ in, int rows, int g0,
-                                      int n_in, int col0, int ncol, int b, int d0, int d1)
+template <int AX, int ROWS>
+__device__ __forceinline__ void stage(float (*S)[kMlPad], const float* __restrict__ in, int g0, int n_in,
+                                      int col0, int ncol, int b, int d0, int d1)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (AX == 0) {
-        // warp w loads lines w, w + 8, ...; lanes run along the line
-        for (int l = warp; l < 32; l += 8) {
+        // warp w loads lines w, w + 8, w + 16, w + 24; lanes run along the line
+        constexpr int PER = (ROWS + 31) / 32;
+        float v[4][PER];
+        #pragma unroll
+        for (int li = 0; li < 4; ++li) {
+            const int l = warp + 8 * li;
             const bool ok = col0 + l < ncol;
-            for (int r = lane; r < rows; r += 32)
-                S[r][l] = ok ? in[offs<0>(col0 + l, wrap(g0 + r, n_in), b, d0, d1, n_in)] : 0.f;
+            #pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int r = lane + 32 * k;
+                v[li][k] = ok && r < ROWS ? in[offs<0>(col0 + l, wrap(g0 + r, n_in), b, d0, d1, n_in)] : 0.f;
+            }
         }
+        #pragma unroll
+        for (int li = 0; li < 4; ++li)
+            #pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (lane + 32 * k < ROWS) S[lane + 32 * k][warp + 8 * li] = v[li][k];
     } else {
+        constexpr int PER = (ROWS + 7) / 8;
         const bool ok = col0 + lane < ncol;
-        for (int r = warp; r < rows; r += 8)
-            S[r][lane] = ok ? in[offs<AX>(col0 + lane, wrap(g0 + r, n_in), b, d0, d1, n_in)] : 0.f;
+        float v[PER];
+        #pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int r = warp + 8 * k;
+            v[k] = ok && r < ROWS ? in[offs<AX>(col0 + lane, wrap(g0 + r, n_in), b, d0, d1, n_in)] : 0.f;
+        }
+        #pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (warp + 8 * k < ROWS) S[warp + 8 * k][lane] = v[k];
     }
 }
 
@@ -124,7 +144,7 @@ __global__ void __launch_bounds__(256) k_ml_restrict(const float* __restrict__ i
     const int n_out = n_in / 2;
     const int col0 = blockIdx.x * 32, a0 = blockIdx.y * kMlCh, b = blockIdx.z;
     // outputs a0 .. a0 + 31 read fine rows 2 a0 - T .. 2 (a0 + 31) + T
-    stage<AX>(S, in, kMlWinR, 2 * a0 - kMlT, n_in, col0, ncol, b, d0, d1);
+    stage<AX, kMlWinR>(S, in, 2 * a0 - kMlT, n_in, col0, ncol, b, d0, d1);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -152,7 +172,7 @@ __global__ void __launch_bounds__(256) k_ml_prolong(const float* __restrict__ in
     const int col0 = blockIdx.x * 32, a0 = blockIdx.y * kMlCh, b = blockIdx.z;
     // fine outputs a0 .. a0 + 31 (a0 even) read coarse rows a0 / 2 - T / 2 .. a0 / 2 + 15 + T / 2
     const int G0 = a0 / 2 - kMlT / 2;
-    stage<AX>(S, in, kMlWinP, G0, n_in, col0, ncol, b, d0, d1);
+    stage<AX, kMlWinP>(S, in, G0, n_in, col0, ncol, b, d0, d1);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};

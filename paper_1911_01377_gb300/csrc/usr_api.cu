@@ -22,7 +22,7 @@
 using usr::Plan;
 
 // profiling events of one evaluation (stage boundaries on the two streams)
-constexpr int kProfEvents = 11;
+constexpr int kProfEvents = 12;
 
 /* Host-side NVTX range around the enqueueing of one stage (no cost unless a tool is attached). */
 struct NvtxRange {
@@ -30,6 +30,19 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
     NvtxRange(const NvtxRange&) = delete;
     NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+/* One tensor-core convolution (three passes): split operands (hi, lo), B tables and tensor maps per pass, the
+   per-term means of the x and y kernels. */
+struct TcConv {
+    bool bf16 = false;
+    void *rho_hi = nullptr, *rho_lo = nullptr, *X_hi = nullptr, *X_lo = nullptr, *Y_hi = nullptr, *Y_lo = nullptr;
+    void* Bt_hi[3] = {nullptr, nullptr, nullptr};
+    void* Bt_lo[3] = {nullptr, nullptr, nullptr};
+    float* mu = nullptr;
+    usr::ConvTcMaps maps[3];
+    usr::ConvTcArgs targs[3];
+    int tbatches[3] = {0, 0, 0};
 };
 
 struct usr_ctx {
@@ -60,13 +73,10 @@ struct usr_ctx {
     // spreading tiles and the per-axis tile tables
     float* d_tilebuf = nullptr;
     int* d_tab[3] = {nullptr, nullptr, nullptr};
-    // tensor-core convolutions: split operands (hi, lo), B tables per pass, per-term means
+    // tensor-core convolutions: the fine grid's (TF32x3 or BF16x3) and, with the multilevel form, the coarse
+    // grid's (TF32x3)
     bool tc = false, tc_bf16 = false;
-    void *d_rho_hi = nullptr, *d_rho_lo = nullptr, *d_X_hi = nullptr, *d_X_lo = nullptr;
-    void *d_Y_hi = nullptr, *d_Y_lo = nullptr;
-    void* d_Bt_hi[3] = {nullptr, nullptr, nullptr};
-    void* d_Bt_lo[3] = {nullptr, nullptr, nullptr};
-    float* d_mu = nullptr;
+    TcConv tcf, tcc;
     double* d_ktab = nullptr;            // 1D kernels, means and scales of the plan (table-build input)
     // virial: per strain component (xx yy zz xy xz yz) FP32 tables {Bx, Ay, Az, wx, wy, wz} and their input
     bool vir = false;
@@ -83,9 +93,7 @@ struct usr_ctx {
     double* d_cktab = nullptr;
     float* d_ctab[6] = {};
     float* d_mlbuf = nullptr;
-    usr::ConvTcMaps maps[3];
-    usr::ConvTcArgs targs[3];
-    int tbatches[3] = {0, 0, 0};
+    bool ml_tc = false;            // coarse passes on the tensor cores (else the FP32 tables above)
     // allocated bytes of every device buffer (buffers only grow), and the
     // pinned staging area of the table uploads with the event of its last use
     std::unordered_map<void**, size_t> cap;
@@ -94,6 +102,7 @@ struct usr_ctx {
     cudaEvent_t stage_ev = nullptr;
     // host-buffer staging and inspection
     float4 *d_in = nullptr, *d_out = nullptr, *d_near_dbg = nullptr, *d_far_dbg = nullptr;
+    float4* d_far4 = nullptr;      // far part per sorted atom (gather -> combination)
     bool keep_parts = false;
     bool inject_timeout = false;
     int near_ctas_per_sm = 0;      // persistent pair-kernel CTAs per SM (0: as many as fit)   // the next evaluation's first tensor-core pass waits on a barrier nothing completes
@@ -132,12 +141,16 @@ void free_all(usr_ctx* c)
                     c->d_pstart, c->d_cidx, c->d_ccell, c->d_cpos, c->d_bblo, c->d_bbhi,
                     c->d_wpos, c->d_spos, c->d_nacc, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
-                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_tilebuf,
-                    c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_rho_hi, c->d_rho_lo, c->d_X_hi, c->d_X_lo,
-                    c->d_Y_hi, c->d_Y_lo, c->d_Bt_hi[0], c->d_Bt_hi[1], c->d_Bt_hi[2], c->d_Bt_lo[0],
-                    c->d_Bt_lo[1], c->d_Bt_lo[2], c->d_mu, c->d_psi_partial, c->d_psi_mean, c->d_ktab};
+                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_far4, c->d_tilebuf,
+                    c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_psi_partial, c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (TcConv* t : {&c->tcf, &c->tcc}) {
+        void* tp[] = {t->rho_hi, t->rho_lo, t->X_hi, t->X_lo, t->Y_hi, t->Y_lo, t->Bt_hi[0], t->Bt_hi[1],
+                      t->Bt_hi[2], t->Bt_lo[0], t->Bt_lo[1], t->Bt_lo[2], t->mu};
+        for (void* p : tp)
+            if (p) cudaFree(p);
+    }
     void* vptrs[] = {c->d_vktab, c->d_psiv, c->d_rho32, c->d_vnear, c->d_vdot, c->d_vpart, c->d_W,
                      c->d_cktab, c->d_mlbuf};
     for (float* p : c->d_ctab)
@@ -254,10 +267,10 @@ double usr::plan_device_bytes(const Plan& P)
     const double nmax = std::max(nx, std::max(ny, nz));
     double b = 4096 + 4 * (ncell + 1) * 3 + 16 * ncl * 8 + 4 * ncl * 8 + 4 * ncl + 32 * ncl;   // cells, clusters
     b += 8 * (3 * N * nmax + 4 * N);                                               // 1D kernel tables
-    b += na * (4 * 4 + 16 * 6 + 32);                                               // per-atom arrays
+    b += na * (4 * 4 + 16 * 7 + 32);                                               // per-atom arrays
     const double ngr = near_max_groups((int)na, (int)ncell);
     b += 8 * (ncell + 1) + 4 * ngr + 4;                                            // pair-kernel groups
-    b += 4 * G + 8 * nsb * 5 + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
+    b += 4 * G + 8 * (nsb * 3 + kCombineBlocks) + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
     if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
@@ -267,9 +280,21 @@ double usr::plan_device_bytes(const Plan& P)
     if (P.Nc > 0) {   // multilevel: weights, coarse tables and their input, scratch, FP32 rho copy (tensor cores)
         const double Nc = P.Nc, cx = P.nc[0], cy = P.nc[1], cz = P.nc[2], Gc = cx * cy * cz;
         const double cmax = std::max(cx, std::max(cy, cz));
+        const bool mtc = tc && P.nc[0] % 4 == 0 && P.nc[1] % 4 == 0 && P.nc[2] % 4 == 0;
         b += 8 * (3 * Nc * cmax + 4 * Nc);
-        b += 4 * Nc * (cx * cx + cy * cy + cz * cz + cx + cy + cz);
-        b += 4 * (std::max(nz * ny * cx, cz * cy * nx) + std::max(nz * cy * cx, cz * ny * nx) + Gc * (2 + 2 * Nc));
+        b += 4 * (std::max(nz * ny * cx, cz * cy * nx) + std::max(nz * cy * cx, cz * ny * nx));
+        if (mtc) {   // TF32x3 coarse passes: split operands, B tables, means, coarse psi
+            b += 4 * Gc * 2 * (1 + 2 * Nc) + 8 * Nc + 4 * Gc;
+            const double n_out[3] = {cx, cy, cz}, K[3] = {cx, cy, Nc * cz}, bat[3] = {Nc, Nc, 1};
+            for (int p = 0; p < 3; ++p) {
+                const double nt = std::floor((n_out[p] + 1 + 255) / 256);
+                const double cols = std::ceil(n_out[p] / nt);
+                const double NT = std::ceil((cols + 1) / 16) * 16;
+                b += 2 * 4 * bat[p] * nt * NT * K[p];
+            }
+        } else {
+            b += 4 * Nc * (cx * cx + cy * cy + cz * cz + cx + cy + cz) + 4 * Gc * (2 + 2 * Nc);
+        }
         if (tc && !P.p.virial) b += 4 * G;
     }
     if (!tc) {
@@ -289,6 +314,82 @@ double usr::plan_device_bytes(const Plan& P)
 }
 
 namespace {
+
+/*
+ * Buffers, tile shapes and tensor maps of a tensor-core convolution of N terms on an nx x ny x nz grid
+ * (BF16x3 or TF32x3); its last pass writes FP32 into psi.  mu: the x then the y kernel mean of each term.
+ */
+usr_status setup_tc(usr_ctx* c, TcConv& t, bool bf, int N, int nx, int ny, int nz, const std::vector<float>& mu,
+                    float* psi, Staged& up)
+{
+    usr_status s = USR_OK;
+    const size_t es = bf ? 2 : 4, G = (size_t)nx * ny * nz;
+    t.bf16 = bf;
+    void** bufs[6] = {&t.rho_hi, &t.rho_lo, &t.X_hi, &t.X_lo, &t.Y_hi, &t.Y_lo};
+    for (int b = 0; b < 6; ++b)
+        if ((s = ensure(c, bufs[b], es * G * (b < 2 ? 1 : (size_t)N))) != USR_OK) return s;
+    if ((s = ensure(c, (void**)&t.mu, sizeof(float) * 2 * N)) != USR_OK) return s;
+    up.add(t.mu, mu.data(), mu.size());
+    const int n_out[3] = {nx, ny, nz};
+    const int Ks[3] = {nx, ny, N * nz};
+    const int lines[3] = {ny * nz, nx * nz, ny * nx};
+    const int batches[3] = {N, N, 1};
+    const long long a_rows[3] = {(long long)ny * nz, (long long)N * nx * nz, (long long)ny * nx};
+    for (int ps = 0; ps < 3; ++ps) {
+        usr::ConvTcArgs& a = t.targs[ps];
+        std::memset(&a, 0, sizeof(a));
+        tc_shape(a, n_out[ps], Ks[ps], bf);
+        const size_t nB = (size_t)batches[ps] * a.ntiles * a.NT * a.K;
+        if ((s = ensure(c, &t.Bt_hi[ps], es * nB)) != USR_OK || (s = ensure(c, &t.Bt_lo[ps], es * nB)) != USR_OK)
+            return s;
+    }
+    void* a_hi[3] = {t.rho_hi, t.X_hi, t.Y_hi};
+    void* a_lo[3] = {t.rho_lo, t.X_lo, t.Y_lo};
+    void* o_hi[3] = {t.X_hi, t.Y_hi, psi};
+    void* o_lo[3] = {t.X_lo, t.Y_lo, nullptr};
+    for (int ps = 0; ps < 3; ++ps) {
+        usr::ConvTcArgs& a = t.targs[ps];
+        a.pass = ps + 1;
+        a.lines = lines[ps];
+        a.a_rows_per_batch = ps == 1 ? nx * nz : 0;
+        a.nterms = N;
+        a.nx = nx;
+        a.ny = ny;
+        a.nz = nz;
+        a.mu = ps == 0 ? t.mu : (ps == 1 ? t.mu + N : nullptr);
+        a.out_hi = o_hi[ps];
+        a.out_lo = o_lo[ps];
+        a.status = c->d_status;
+        a.out_elems = ps == 2 ? (long long)G : (long long)G * (long long)N;
+        t.tbatches[ps] = batches[ps];
+        const long long b_rows = (long long)batches[ps] * a.ntiles * a.NT;
+        if ((s = usr::make_tmap(&t.maps[ps].a_hi, a_hi[ps], bf, a_rows[ps], a.K, 128)) ||
+            (s = usr::make_tmap(&t.maps[ps].a_lo, a_lo[ps], bf, a_rows[ps], a.K, 128)) ||
+            (s = usr::make_tmap(&t.maps[ps].b_hi, t.Bt_hi[ps], bf, b_rows, a.K, a.NT)) ||
+            (s = usr::make_tmap(&t.maps[ps].b_lo, t.Bt_lo[ps], bf, b_rows, a.K, a.NT)))
+            return s;
+    }
+    return USR_OK;
+}
+
+/* Enqueue the three passes of a tensor-core convolution on st (the first may carry the test-only wait). */
+template <typename F>
+void run_tc(const TcConv& t, bool inject, cudaStream_t st, F after)
+{
+    for (int p = 0; p < 3; ++p) {
+        usr::ConvTcArgs ta = t.targs[p];
+        ta.inject_wait_ns = (p == 0 && inject) ? 1000000ull : 0ull;   // 1 ms, one evaluation
+        usr::launch_conv_tc(t.bf16, t.maps[p], ta, t.tbatches[p], st);
+        after(p);
+    }
+}
+
+/* The coarse grid's scratch: t1 | t2 | rho_c | X_c | Y_c | psi_c (rho_c, X_c, Y_c only for FP32 passes). */
+float* ml_psi_c(usr_ctx* c)
+{
+    const size_t Gc = (size_t)c->plan.nc[0] * c->plan.nc[1] * c->plan.nc[2];
+    return c->d_mlbuf + c->ml_t1 + c->ml_t2 + (c->ml_tc ? 0 : Gc * (1 + 2 * (size_t)c->mlN));
+}
 
 /*
  * Make `c` evaluate the system described by p: plan on the host, grow device
@@ -341,7 +442,8 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_psi, fl * G);
     ENSURE(c->d_spread_partial, db * nsb);
     ENSURE(c->d_mean, db);
-    ENSURE(c->d_gather_partial, db * nsb * 4);
+    ENSURE(c->d_gather_partial, db * (nsb * 2 + usr::kCombineBlocks));
+    ENSURE(c->d_far4, f4 * na);
     ENSURE(c->d_energy, db * 4);
     ENSURE(c->d_counters, sizeof(unsigned int) * 4);
     ENSURE(c->d_psi_partial, db * usr::kGridMeanBlocks);
@@ -424,9 +526,13 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
         }
         up.add(c->d_vktab, kt.data(), kt.size());
     }
-    // multilevel: transfer weights (FP32, three axes) and the coarse grid's 1D kernels, in the fine layout
+    // multilevel: transfer weights (FP32, three axes) and the coarse grid's 1D kernels, in the fine layout.
+    // With tensor-core fine passes the coarse passes run on the tensor cores too, in TF32x3 whatever the fine
+    // form (the wide terms' near-constant parts need more than the 16 bits of BF16x3), when every coarse
+    // extent is a multiple of 4 (16-byte rows of the tensor maps); else in FP32.
     usr::ConvTableArgs ctab{};
     c->mlN = P.Nc;
+    c->ml_tc = P.Nc > 0 && c->tc && P.nc[0] % 4 == 0 && P.nc[1] % 4 == 0 && P.nc[2] % 4 == 0;
     if (P.Nc > 0) {
         const size_t Nc = (size_t)P.Nc;
         const int cx = P.nc[0], cy = P.nc[1], cz = P.nc[2];
@@ -447,15 +553,17 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
             }
         for (size_t j = 0; j < Nc; ++j) kt[3 * Nc * cmax + 3 * Nc + j] = P.scale_c[j];
         up.add(c->d_cktab, kt.data(), kt.size());
-        ENSURE(c->d_ctab[0], fl * cx * Nc * cx);
-        ENSURE(c->d_ctab[1], fl * Nc * cy * cy);
-        ENSURE(c->d_ctab[2], fl * cz * Nc * cz);
-        ENSURE(c->d_ctab[3], fl * Nc * cx);
-        ENSURE(c->d_ctab[4], fl * Nc * cy);
-        ENSURE(c->d_ctab[5], fl * Nc * cz);
+        if (!c->ml_tc) {
+            ENSURE(c->d_ctab[0], fl * cx * Nc * cx);
+            ENSURE(c->d_ctab[1], fl * Nc * cy * cy);
+            ENSURE(c->d_ctab[2], fl * cz * Nc * cz);
+            ENSURE(c->d_ctab[3], fl * Nc * cx);
+            ENSURE(c->d_ctab[4], fl * Nc * cy);
+            ENSURE(c->d_ctab[5], fl * Nc * cz);
+        }
         c->ml_t1 = std::max((size_t)nz * ny * cx, (size_t)cz * cy * nx);
         c->ml_t2 = std::max((size_t)nz * cy * cx, (size_t)cz * ny * nx);
-        ENSURE(c->d_mlbuf, fl * (c->ml_t1 + c->ml_t2 + Gc * (2 + 2 * Nc)));
+        ENSURE(c->d_mlbuf, fl * (c->ml_t1 + c->ml_t2 + (c->ml_tc ? Gc : Gc * (2 + 2 * Nc))));
         if (c->tc) ENSURE(c->d_rho32, fl * G);
         ctab.N = (int)Nc;
         ctab.n[0] = cx;
@@ -492,60 +600,22 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     }
     c->grid.psi_mean = c->d_psi_mean;
     if (c->tc) {
-        const bool bf = c->tc_bf16;
-        const size_t es = bf ? 2 : 4;
-        ENSURE(c->d_rho_hi, es * G);
-        ENSURE(c->d_rho_lo, es * G);
-        ENSURE(c->d_X_hi, es * G * N);
-        ENSURE(c->d_X_lo, es * G * N);
-        ENSURE(c->d_Y_hi, es * G * N);
-        ENSURE(c->d_Y_lo, es * G * N);
-        ENSURE(c->d_mu, fl * 2 * N);
         std::vector<float> mu(2 * N);
         for (size_t j = 0; j < N; ++j) {
             mu[j] = (float)P.mu[0][j];
             mu[N + j] = (float)P.mu[1][j];
         }
-        up.add(c->d_mu, mu.data(), mu.size());
-        const int n_out[3] = {nx, ny, nz};
-        const int Ks[3] = {nx, ny, (int)N * nz};
-        const int lines[3] = {ny * nz, nx * nz, ny * nx};
-        const int batches[3] = {(int)N, (int)N, 1};
-        const long long a_rows[3] = {(long long)ny * nz, (long long)N * nx * nz, (long long)ny * nx};
-        for (int ps = 0; ps < 3; ++ps) {
-            usr::ConvTcArgs& a = c->targs[ps];
-            std::memset(&a, 0, sizeof(a));
-            tc_shape(a, n_out[ps], Ks[ps], bf);
-            const size_t nB = (size_t)batches[ps] * a.ntiles * a.NT * a.K;
-            ENSURE(c->d_Bt_hi[ps], es * nB);
-            ENSURE(c->d_Bt_lo[ps], es * nB);
+        if ((s = setup_tc(c, c->tcf, c->tc_bf16, (int)N, nx, ny, nz, mu, c->d_psi, up)) != USR_OK) return s;
+    }
+    if (c->ml_tc) {
+        const int Nc = P.Nc;
+        std::vector<float> mu(2 * Nc);
+        for (int j = 0; j < Nc; ++j) {
+            mu[j] = (float)P.mu_c[0][j];
+            mu[Nc + j] = (float)P.mu_c[1][j];
         }
-        void* a_hi[3] = {c->d_rho_hi, c->d_X_hi, c->d_Y_hi};
-        void* a_lo[3] = {c->d_rho_lo, c->d_X_lo, c->d_Y_lo};
-        void* o_hi[3] = {c->d_X_hi, c->d_Y_hi, c->d_psi};
-        void* o_lo[3] = {c->d_X_lo, c->d_Y_lo, nullptr};
-        for (int ps = 0; ps < 3; ++ps) {
-            usr::ConvTcArgs& a = c->targs[ps];
-            a.pass = ps + 1;
-            a.lines = lines[ps];
-            a.a_rows_per_batch = ps == 1 ? nx * nz : 0;
-            a.nterms = (int)N;
-            a.nx = nx;
-            a.ny = ny;
-            a.nz = nz;
-            a.mu = ps == 0 ? c->d_mu : (ps == 1 ? c->d_mu + N : nullptr);
-            a.out_hi = o_hi[ps];
-            a.out_lo = o_lo[ps];
-            a.status = c->d_status;
-            a.out_elems = ps == 2 ? (long long)G : (long long)G * (long long)N;
-            c->tbatches[ps] = batches[ps];
-            const long long b_rows = (long long)batches[ps] * a.ntiles * a.NT;
-            if ((s = usr::make_tmap(&c->maps[ps].a_hi, a_hi[ps], bf, a_rows[ps], a.K, 128)) ||
-                (s = usr::make_tmap(&c->maps[ps].a_lo, a_lo[ps], bf, a_rows[ps], a.K, 128)) ||
-                (s = usr::make_tmap(&c->maps[ps].b_hi, c->d_Bt_hi[ps], bf, b_rows, a.K, a.NT)) ||
-                (s = usr::make_tmap(&c->maps[ps].b_lo, c->d_Bt_lo[ps], bf, b_rows, a.K, a.NT)))
-                return s;
-        }
+        if ((s = setup_tc(c, c->tcc, false, Nc, P.nc[0], P.nc[1], P.nc[2], mu, ml_psi_c(c), up)) != USR_OK)
+            return s;
     }
 #undef ENSURE
     {   // what the context holds (buffers only grow, so this can exceed the plan's own need)
@@ -574,10 +644,9 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     if (cudaEventRecord(c->stage_ev, st) != cudaSuccess) return USR_ERR_CUDA;
     // convolution tables, built on the device from the uploaded kernels
     if (c->tc) {
-        const int batches[3] = {(int)N, (int)N, 1};
         for (int ps = 0; ps < 3; ++ps)
-            usr::launch_tc_table(c->tc_bf16, tab, ps + 1, batches[ps], c->targs[ps], c->d_Bt_hi[ps], c->d_Bt_lo[ps],
-                                 st);
+            usr::launch_tc_table(c->tc_bf16, tab, ps + 1, c->tcf.tbatches[ps], c->tcf.targs[ps], c->tcf.Bt_hi[ps],
+                                 c->tcf.Bt_lo[ps], st);
     } else {
         usr::launch_fp32_tables(tab, c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz, st);
     }
@@ -585,7 +654,11 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
         for (int cmp = 0; cmp < 6; ++cmp)
             usr::launch_fp32_tables(vtab[cmp], c->d_vtab[cmp][0], c->d_vtab[cmp][1], c->d_vtab[cmp][2],
                                     c->d_vtab[cmp][3], c->d_vtab[cmp][4], c->d_vtab[cmp][5], st);
-    if (c->mlN > 0)
+    if (c->ml_tc)
+        for (int ps = 0; ps < 3; ++ps)
+            usr::launch_tc_table(false, ctab, ps + 1, c->tcc.tbatches[ps], c->tcc.targs[ps], c->tcc.Bt_hi[ps],
+                                 c->tcc.Bt_lo[ps], st);
+    else if (c->mlN > 0)
         usr::launch_fp32_tables(ctab, c->d_ctab[0], c->d_ctab[1], c->d_ctab[2], c->d_ctab[3], c->d_ctab[4],
                                 c->d_ctab[5], st);
     return check_launch();
@@ -759,9 +832,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         c->vir_valid = c->vir;
         return USR_OK;
     }
-    // stage boundaries: on the caller's stream 0 start, 1 cell list done, 2 pair kernel done, 9 gather
-    // may start (the far chain joined), 10 end; on the side stream 3 start, 4 spread done, 5-7 passes
-    // x, y, z done, 8 psi mean done
+    // stage boundaries: on the caller's stream 0 start, 1 cell list done, 2 pair kernel done, 9 the
+    // combination may start (the far chain joined), 10 end; on the side stream 3 start, 4 spread done, 5-7
+    // passes x, y, z done, 8 psi mean done, 11 far gather done
     auto mark = [&](int k, cudaStream_t s) {
         if (c->prof == 1 || (c->prof == 2 && (k == 1 || k == 2))) cudaEventRecord(c->ev[k], s);
     };
@@ -786,19 +859,14 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         mark(3, sd);
         if (c->tc)
             usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, c->tc_bf16 ? 2 : 1,
-                               c->d_rho_hi, c->d_rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status,
+                               c->tcf.rho_hi, c->tcf.rho_lo, c->d_spread_partial, c->d_counters, c->d_mean, c->d_status,
                                sd, (c->vir || c->mlN > 0) ? c->d_rho32 : nullptr);
         else
             usr::launch_spread(P.P, c->d_spos, c->d_cell_start, c->grid, c->d_tilebuf, 0, c->d_rho, nullptr,
                                c->d_spread_partial, c->d_counters, c->d_mean, c->d_status, sd);
         mark(4, sd);
         if (c->tc) {
-            for (int p = 0; p < 3; ++p) {
-                usr::ConvTcArgs ta = c->targs[p];
-                ta.inject_wait_ns = (p == 0 && c->inject_timeout) ? 1000000ull : 0ull;   // 1 ms, one evaluation
-                usr::launch_conv_tc(c->tc_bf16, c->maps[p], ta, c->tbatches[p], sd);
-                mark(5 + p, sd);
-            }
+            run_tc(c->tcf, c->inject_timeout, sd, [&](int k) { mark(5 + k, sd); });
             c->inject_timeout = false;
         } else {
             float* const t[6] = {c->d_Bx, c->d_Ay, c->d_Az, c->d_wx, c->d_wy, c->d_wz};
@@ -810,16 +878,26 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
             const size_t Gc = (size_t)Q.nc[0] * Q.nc[1] * Q.nc[2];
             float* t1 = c->d_mlbuf;
             float* t2 = t1 + c->ml_t1;
-            float* rc = t2 + c->ml_t2;
-            float* Xc = rc + Gc;
-            float* Yc = Xc + (size_t)c->mlN * Gc;
-            float* pc = Yc + (size_t)c->mlN * Gc;
-            usr::launch_ml_restrict(c->ml, c->tc ? c->d_rho32 : c->d_rho, t1, t2, rc, nullptr, c->d_status, sd);
-            conv3(Conv3{c->mlN, Q.nc[0], Q.nc[1], Q.nc[2], Xc, Yc}, rc, c->d_ctab, pc, sd, [](int) {});
+            float* pc = ml_psi_c(c);
+            const float* rho = c->tc ? c->d_rho32 : c->d_rho;
+            if (c->ml_tc) {
+                usr::launch_ml_restrict(c->ml, rho, t1, t2, static_cast<float*>(c->tcc.rho_hi),
+                                        static_cast<float*>(c->tcc.rho_lo), c->d_status, sd);
+                run_tc(c->tcc, false, sd, [](int) {});
+            } else {
+                float* rc = t2 + c->ml_t2;
+                float* Xc = rc + Gc;
+                float* Yc = Xc + (size_t)c->mlN * Gc;
+                usr::launch_ml_restrict(c->ml, rho, t1, t2, rc, nullptr, c->d_status, sd);
+                conv3(Conv3{c->mlN, Q.nc[0], Q.nc[1], Q.nc[2], Xc, Yc}, rc, c->d_ctab, pc, sd, [](int) {});
+            }
             usr::launch_ml_prolong(c->ml, pc, t1, t2, c->d_psi, c->d_status, sd);
         }
         usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
         mark(8, sd);
+        usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_psi, c->grid, c->d_far4, c->d_gather_partial,
+                           c->d_status, sd);
+        mark(11, sd);
         if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
     }
     {
@@ -832,10 +910,12 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     if (cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return USR_ERR_CUDA;
     mark(9, st);
     {
-        NvtxRange r("usr: gather + energy");
-        usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_perm, c->d_nacc, c->d_psi, c->grid, out,
-                           c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
-                           c->d_gather_partial, c->d_counters + 1, en, c->d_status, st);
+        NvtxRange r("usr: near + far, energy");
+        const int nfar = usr::tile_blocks(c->grid.tg);
+        usr::launch_combine(n, c->d_spos, c->d_perm, c->d_nacc, c->d_far4, c->grid.F0, nfar, c->d_gather_partial,
+                            out, c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
+                            c->d_gather_partial + 2 * (size_t)nfar, c->d_counters + 1, en, c->max_atoms,
+                            c->d_status, st);
         mark(10, st);
     }
     if (c->vir) {
@@ -1095,8 +1175,9 @@ extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
         return cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]) == cudaSuccess ? USR_OK : USR_ERR_CUDA;
     }
     if (cudaEventSynchronize(c->ev[10]) != cudaSuccess) return USR_ERR_CUDA;
-    // (from, to) event pairs of the stages; the gather stage adds the psi mean (8 - 7) to the gather itself
-    // (10 - 9); the wait for the later of the two branches (between 2 or 8 and 9) is in no stage
+    // (from, to) event pairs of the stages; the gather stage adds the psi mean and the far gather (11 - 7)
+    // to the combination (10 - 9); the wait for the later of the two branches (between 2 or 11 and 9) is in
+    // no stage
     static const int from[USR_NSTAGES] = {0, 1, 3, 4, 5, 6, 9}, to[USR_NSTAGES] = {1, 2, 4, 5, 6, 7, 10};
     for (int k = 0; k < USR_NSTAGES; ++k) {
         float t = 0.f;
@@ -1104,7 +1185,7 @@ extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
         ms[k] = t;
     }
     float gm = 0.f;
-    if (cudaEventElapsedTime(&gm, c->ev[7], c->ev[8]) != cudaSuccess) return USR_ERR_CUDA;
+    if (cudaEventElapsedTime(&gm, c->ev[7], c->ev[11]) != cudaSuccess) return USR_ERR_CUDA;
     ms[USR_NSTAGES - 1] += gm;
     return USR_OK;
 }

@@ -21,6 +21,7 @@ constexpr int kMaxTerms = 16;
 constexpr int kMlT = 16;           // multilevel transfer half-width in fine points: ceil(6 x 2.6)
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
+constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
 
 /*
  * Cell blocks of the spreading / interpolation kernels and their smem tiles.
@@ -282,11 +283,17 @@ usr_status conv_tc_setup(bool bf16, size_t smem);
 void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int batches, cudaStream_t st);
 void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
                       cudaStream_t st);
-void launch_gather(int P, const float4* spos, const int* cell_start, const int* perm,
-                   const unsigned long long* near_acc,
-                   const float* psi, const GridArgs& g, float4* out, float4* near_dbg,
-                   float4* far_dbg, double* partial, unsigned int* counter, double* energy, int* status,
-                   cudaStream_t st);
+/* far part at every sorted atom into far4 (F_far, phi_far), per tile block the E_far and E_self sums into
+   partial[2 b], partial[2 b + 1] */
+void launch_gather(int P, const float4* spos, const int* cell_start, const float* psi, const GridArgs& g,
+                   float4* far4, double* partial, int* status, cudaStream_t st);
+/* near + far in caller order into out (and the parts into near_dbg / far_dbg when non-null); energy[0..3] =
+   total, near, far, self from the per-block E_near sums (partial, kCombineBlocks at most) and the gather's
+   nfar block pairs */
+void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
+                    const float4* far4, float F0, int nfar, const double* far_partial, float4* out,
+                    float4* near_dbg, float4* far_dbg, double* partial, unsigned int* counter, double* energy,
+                    int max_atoms, int* status, cudaStream_t st);
 int tile_blocks(const TileGeom& tg);
 size_t tile_floats(const TileGeom& tg);
 usr_status grid_kernel_setup(size_t smem_bytes);
