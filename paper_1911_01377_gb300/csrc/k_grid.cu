@@ -447,139 +447,110 @@ __device__ __forceinline__ float4 near_part(const unsigned long long* __restrict
                        __ll2float_rn((long long)v.x) * k, __ll2float_rn((long long)v.y) * k);
 }
 
+/*
+ * Far part at every sorted atom (the gather of Sec. V: the spreading Gaussian of the atom against psi,
+ * and its gradient), read straight from psi in global memory: consecutive sorted atoms are neighbours in
+ * space, so a CTA's stencils overlap and hit in L1 / L2.  A CTA takes kGatherAtoms consecutive atoms per
+ * pass, a quad of lanes per atom: lane u of the quad takes the stencil columns x = u, u + 4, ... of every
+ * row, contracting z first.  Writes far4[s] = (-q grad phi, phi_far) and per CTA the E_far, E_self sums.
+ */
+#ifndef USR_GATHER_MINB
+#define USR_GATHER_MINB 2   // CTAs per SM the 8- and 10-point gathers are compiled for (3 spills; measured slower)
+#endif
+
 template <int P>
-__global__ void __launch_bounds__(kThreads, 3) k_gather(const float4* __restrict__ pos,
-                                                        const int* __restrict__ cell_start,
-                                                        const float* __restrict__ psi, GridArgs g,
-                                                        float4* __restrict__ far4, double* __restrict__ partial,
-                                                        int* __restrict__ status)
+__global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gather(const float4* __restrict__ pos, int n,
+                                                     const float* __restrict__ psi, GridArgs g,
+                                                     float4* __restrict__ far4, double* __restrict__ partial,
+                                                     int* __restrict__ status)
 {
     constexpr int H = P / 2;
-    extern __shared__ float4 smem4[];
-    float* tile = reinterpret_cast<float*>(smem4);
-    __shared__ int rs[kMaxRows], pre[kMaxRows + 1];
-    __shared__ double red[kWarps][2];
-    __shared__ float4 sp[kGChunk];                // staged atoms: position/charge
-    __shared__ int si[kGChunk];                   // and sorted index
-    const int Tx = g.tg.T[0], Ty = g.tg.T[1], Tz = g.tg.T[2];
-    const int TXY = Tx * Ty;
-    const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
-    const BlockGeom bg = block_geom(g, blockIdx.x);
-    // stage the psi tile with asynchronous 4-byte copies (many in flight per thread)
-    for (int r = threadIdx.x >> 5; r < Ty * Tz; r += kWarps) {
-        const int ty = r % Ty, tz = r / Ty;
-        const int gy = wrap_once(bg.o[1] + ty, n1), gz = wrap_once(bg.o[2] + tz, n2);
-        const float* src = psi + ((size_t)gz * n1 + gy) * n0;
-        float* dst = tile + (size_t)r * Tx;
-        for (int tx = threadIdx.x & 31; tx < Tx; tx += 32) {
-            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + tx));
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + wrap_once(bg.o[0] + tx, n0))
-                         : "memory");
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    const int natoms = block_rows(g, bg, cell_start, rs, pre);   // contains a barrier
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // four lanes (a quad) per atom, eight atoms per warp: lane u of a quad takes
-    // the stencil columns jx = u, u + 4, ... of every row, contracting z first
     constexpr int NC = (P + 3) / 4;
+    __shared__ double red[kWarps][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, u = lane & 3;
+    const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
+    const long long plane = (long long)n0 * n1;
     CSum qf, qq;                                           // sums of q phi_far, q^2
     const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
-    for (int c0 = 0; c0 < natoms; c0 += kGChunk) {
-        const int nch = min(kGChunk, natoms - c0);
-        __syncthreads();                           // the previous chunk is done
-        for (int a = threadIdx.x; a < nch; a += kThreads) {
-            const int s = block_atom(c0 + a, rs, pre);
-            const bool in = USR_IN_BOUNDS(s, g.max_atoms, status);
-            sp[a] = pos[in ? s : 0];
-            si[a] = in ? s : -1;
+    for (int s0 = blockIdx.x * kGatherAtoms + warp * 8; s0 < n; s0 += gridDim.x * kGatherAtoms) {
+        const int s = s0 + quad;
+        const bool have = s < n;
+        const float4 p = pos[have ? s : s0];
+        const float pc[3] = {p.x, p.y, p.z};
+        int base[3];
+        float tt[3];
+        #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float uu = pc[a] * g.box.gs[a];
+            const float f = floorf(uu);
+            tt[a] = uu - f;
+            base[a] = (int)f - H + 1;
         }
-        __syncthreads();
-        for (int j0 = warp * 8; j0 < nch; j0 += kWarps * 8) {
-            const int j = j0 + quad;
-            const bool have = j < nch;
-            const float4 p = sp[have ? j : j0];
-            const float pc[3] = {p.x, p.y, p.z};
-            int base[3];
-            float tt[3];
-            bool ok = have;
+        float wz[P], dz[P], wx[NC], dx[NC];
+        int zi[P], xo[NC];
+        #pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const float d2 = (float)(k - H + 1) - tt[2];
+            wz[k] = __expf(-d2 * d2 * g.hh[2]);
+            dz[k] = wz[k] * d2 * g.dfac[2];
+            zi[k] = wrap_once(base[2] + k, n2);
+        }
+        #pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const int c = u + 4 * m;
+            const float d0 = (float)(c - H + 1) - tt[0];
+            wx[m] = c < P ? __expf(-d0 * d0 * g.hh[0]) : 0.f;
+            dx[m] = wx[m] * d0 * g.dfac[0];
+            xo[m] = wrap_once(base[0] + (c < P ? c : 0), n0);
+        }
+        float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+        #pragma unroll
+        for (int jy = 0; jy < P; ++jy) {
+            const float d1 = (float)(jy - H + 1) - tt[1];
+            const float wy = __expf(-d1 * d1 * g.hh[1]);
+            const float dy = wy * d1 * g.dfac[1];
+            const int yo = wrap_once(base[1] + jy, n1) * n0;
+            float r0 = 0.f, r1 = 0.f, r2 = 0.f;
             #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float uu = pc[a] * g.box.gs[a];
-                const float f = floorf(uu);
-                tt[a] = uu - f;
-                base[a] = (int)f - H + 1 - bg.o[a];
-                ok = ok && base[a] >= 0 && base[a] + P <= g.tg.T[a];
-            }
-            float aphi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            if (ok) {
-                float wz[P], dz[P], wy[P], dy[P], wx[NC], dx[NC];
+            for (int m = 0; m < NC; ++m) {
+                if (u + 4 * m >= P) continue;
+                const float* col = psi + yo + xo[m];
+                float v[P];
                 #pragma unroll
-                for (int k = 0; k < P; ++k) {
-                    const float d2 = (float)(k - H + 1) - tt[2];
-                    wz[k] = __expf(-d2 * d2 * g.hh[2]);
-                    dz[k] = wz[k] * d2 * g.dfac[2];
-                    const float d1 = (float)(k - H + 1) - tt[1];
-                    wy[k] = __expf(-d1 * d1 * g.hh[1]);
-                    dy[k] = wy[k] * d1 * g.dfac[1];
-                }
+                for (int k = 0; k < P; ++k) v[k] = __ldg(col + (long long)zi[k] * plane);
+                float c0a = 0.f, c0b = 0.f, c1a = 0.f, c1b = 0.f;
                 #pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const float d0 = (float)(u + 4 * m - H + 1) - tt[0];
-                    wx[m] = (u + 4 * m < P) ? __expf(-d0 * d0 * g.hh[0]) : 0.f;
-                    dx[m] = wx[m] * d0 * g.dfac[0];
+                for (int k = 0; k < P; k += 2) {
+                    c0a = fmaf(wz[k], v[k], c0a);
+                    c1a = fmaf(dz[k], v[k], c1a);
+                    c0b = fmaf(wz[k + 1], v[k + 1], c0b);
+                    c1b = fmaf(dz[k + 1], v[k + 1], c1b);
                 }
-                const float* b0 = tile + ((base[2] * Ty + base[1]) * Tx + base[0] + u);
-                #pragma unroll
-                for (int jy = 0; jy < P; ++jy) {
-                    const float* row = b0 + jy * Tx;
-                    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-                    #pragma unroll
-                    for (int m = 0; m < NC; ++m) {
-                        if (u + 4 * m >= P) continue;
-                        const float* col = row + 4 * m;
-                        float v[P];
-                        #pragma unroll
-                        for (int k = 0; k < P; ++k) v[k] = col[k * TXY];
-                        float c0a = 0.f, c0b = 0.f, c1a = 0.f, c1b = 0.f;
-                        #pragma unroll
-                        for (int k = 0; k < P; k += 2) {
-                            c0a = fmaf(wz[k], v[k], c0a);
-                            c1a = fmaf(dz[k], v[k], c1a);
-                            c0b = fmaf(wz[k + 1], v[k + 1], c0b);
-                            c1b = fmaf(dz[k + 1], v[k + 1], c1b);
-                        }
-                        const float cz0 = c0a + c0b, cz1 = c1a + c1b;
-                        r0 = fmaf(wx[m], cz0, r0);
-                        r1 = fmaf(dx[m], cz0, r1);
-                        r2 = fmaf(wx[m], cz1, r2);
-                    }
-                    aphi = fmaf(wy[jy], r0, aphi);
-                    ax = fmaf(wy[jy], r1, ax);
-                    ay = fmaf(dy[jy], r0, ay);
-                    az = fmaf(wy[jy], r2, az);
-                }
-            } else if (have && u == 0) {
-                atomicOr(status, 2);          // cannot happen for wrapped positions
+                const float cz0 = c0a + c0b, cz1 = c1a + c1b;
+                r0 = fmaf(wx[m], cz0, r0);
+                r1 = fmaf(dx[m], cz0, r1);
+                r2 = fmaf(wx[m], cz1, r2);
             }
-            // the four lanes of a quad hold disjoint partial sums
-            #pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-                aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
-                ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                ay += __shfl_xor_sync(0xffffffffu, ay, o);
-                az += __shfl_xor_sync(0xffffffffu, az, o);
-            }
-            aphi -= phi_dc;
-            if (have && u == 0 && si[j] >= 0) {
-                const float qi = p.w;
-                far4[si[j]] = make_float4(-qi * ax, -qi * ay, -qi * az, aphi);
-                qf.add_product(qi, aphi);
-                qq.add_product(qi, qi);
-            }
+            aphi = fmaf(wy, r0, aphi);
+            ax = fmaf(wy, r1, ax);
+            ay = fmaf(dy, r0, ay);
+            az = fmaf(wy, r2, az);
+        }
+        // the four lanes of a quad hold disjoint partial sums
+        #pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+        }
+        aphi -= phi_dc;
+        if (have && u == 0 && USR_IN_BOUNDS(s, g.max_atoms, status)) {
+            const float qi = p.w;
+            far4[s] = make_float4(-qi * ax, -qi * ay, -qi * az, aphi);
+            qf.add_product(qi, aphi);
+            qq.add_product(qi, qi);
         }
     }
     // per-warp sums in a fixed order (lanes 0, 4, ..., 28 hold atoms), then per block: E_far, E_self
@@ -676,7 +647,6 @@ template <int P>
 static void set_smem(size_t bytes)
 {
     cudaFuncSetAttribute(k_spread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(k_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 /* Allow every stencil variant the largest tile a plan may choose. */
@@ -719,16 +689,17 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
         k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr, status);
 }
 
-#define USR_GATHER_CASE(PP)                                                                                  \
-    case PP:                                                                                                 \
-        k_gather<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, psi, g, far4, partial, status);           \
+#define USR_GATHER_CASE(PP)                                                                \
+    case PP:                                                                               \
+        k_gather<PP><<<nb, kThreads, 0, st>>>(spos, n, psi, g, far4, partial, status);     \
         break;
 
-void launch_gather(int P, const float4* spos, const int* cell_start, const float* psi, const GridArgs& g,
-                   float4* far4, double* partial, int* status, cudaStream_t st)
+int gather_blocks(int n) { return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms)); }
+
+void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
+                   double* partial, int* status, cudaStream_t st)
 {
-    const int nb = tile_blocks(g.tg);
-    const size_t smem = sizeof(float) * tile_floats(g.tg);
+    const int nb = gather_blocks(n);
     switch (P) {
         USR_GATHER_CASE(8)
         USR_GATHER_CASE(10)

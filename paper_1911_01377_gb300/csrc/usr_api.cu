@@ -270,7 +270,8 @@ double usr::plan_device_bytes(const Plan& P)
     b += na * (4 * 4 + 16 * 7 + 32);                                               // per-atom arrays
     const double ngr = near_max_groups((int)na, (int)ncell);
     b += 8 * (ncell + 1) + 4 * ngr + 4;                                            // pair-kernel groups
-    b += 4 * G + 8 * (nsb * 3 + kCombineBlocks) + 8 * 8 + 8 * kGridMeanBlocks + 4 * nsb * tile_floats(P.tile);
+    b += 4 * G + 8 * (nsb + 2 * kGatherBlocks + kCombineBlocks) + 8 * 8 + 8 * kGridMeanBlocks +
+         4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
     if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
@@ -442,7 +443,7 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_psi, fl * G);
     ENSURE(c->d_spread_partial, db * nsb);
     ENSURE(c->d_mean, db);
-    ENSURE(c->d_gather_partial, db * (nsb * 2 + usr::kCombineBlocks));
+    ENSURE(c->d_gather_partial, db * (2 * usr::kGatherBlocks + usr::kCombineBlocks));
     ENSURE(c->d_far4, f4 * na);
     ENSURE(c->d_energy, db * 4);
     ENSURE(c->d_counters, sizeof(unsigned int) * 4);
@@ -895,8 +896,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         }
         usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
         mark(8, sd);
-        usr::launch_gather(P.P, c->d_spos, c->d_cell_start, c->d_psi, c->grid, c->d_far4, c->d_gather_partial,
-                           c->d_status, sd);
+        usr::launch_gather(P.P, n, c->d_spos, c->d_psi, c->grid, c->d_far4, c->d_gather_partial, c->d_status, sd);
         mark(11, sd);
         if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
     }
@@ -911,7 +911,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     mark(9, st);
     {
         NvtxRange r("usr: near + far, energy");
-        const int nfar = usr::tile_blocks(c->grid.tg);
+        const int nfar = usr::gather_blocks(n);
         usr::launch_combine(n, c->d_spos, c->d_perm, c->d_nacc, c->d_far4, c->grid.F0, nfar, c->d_gather_partial,
                             out, c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
                             c->d_gather_partial + 2 * (size_t)nfar, c->d_counters + 1, en, c->max_atoms,

@@ -22,6 +22,8 @@ constexpr int kMlT = 16;           // multilevel transfer half-width in fine poi
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
+constexpr int kGatherAtoms = 64;       // atoms per gather CTA pass (8 warps x 8 quads)
+constexpr int kGatherBlocks = 1216;    // gather CTAs at most (eight per SM)
 
 /*
  * Cell blocks of the spreading / interpolation kernels and their smem tiles.
@@ -283,10 +285,11 @@ usr_status conv_tc_setup(bool bf16, size_t smem);
 void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int batches, cudaStream_t st);
 void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
                       cudaStream_t st);
-/* far part at every sorted atom into far4 (F_far, phi_far), per tile block the E_far and E_self sums into
-   partial[2 b], partial[2 b + 1] */
-void launch_gather(int P, const float4* spos, const int* cell_start, const float* psi, const GridArgs& g,
-                   float4* far4, double* partial, int* status, cudaStream_t st);
+/* far part at each of the n sorted atoms into far4 (F_far, phi_far), per CTA b the E_far and E_self sums into
+   partial[2 b], partial[2 b + 1]; gather_blocks(n) CTAs (kGatherBlocks at most) */
+void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
+                   double* partial, int* status, cudaStream_t st);
+int gather_blocks(int n);
 /* near + far in caller order into out (and the parts into near_dbg / far_dbg when non-null); energy[0..3] =
    total, near, far, self from the per-block E_near sums (partial, kCombineBlocks at most) and the gather's
    nfar block pairs */
