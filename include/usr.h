@@ -379,9 +379,11 @@ usr_status usr_set_profiling(usr_ctx* ctx, int on);
 /*
  * Milliseconds of each stage of the last profiled usr_eval (synchronises).
  * ms must hold USR_NSTAGES floats; with profiling level 2 only the near stage
- * (index 1) is measured and the others read 0.  The far chain (spread, conv_x/y/z, and the
- * psi mean, counted in gather) runs on the context's own high-priority stream,
- * concurrently with the near stage on the caller's stream, so the stages can
+ * (index 1) is measured and the others read 0.  The far chain (spread,
+ * conv_x/y/z, then the multilevel coarse steps and the far gather, both
+ * counted in gather) runs on the context's own high-priority stream,
+ * concurrently with the near stage on the caller's stream; gather also counts
+ * the near + far combination after the two streams join.  So the stages can
  * add up to more than the evaluation's duration.
  */
 usr_status usr_stage_times(usr_ctx* ctx, float* ms);

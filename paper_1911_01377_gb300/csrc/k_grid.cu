@@ -393,13 +393,6 @@ __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __r
     }
 }
 
-void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
-                      cudaStream_t st)
-{
-    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
-    k_grid_mean<<<kGridMeanBlocks, 256, 0, st>>>(G, psi, nullptr, 1.0 / (double)G, partial, counter, mean);
-}
-
 /* out = scale * sum_g a_g b_g in FP64, fixed order (the virial's grid dot products). */
 void launch_grid_dot(const GridArgs& g, const float* a, const float* b, double scale, double* partial,
                      unsigned int* counter, double* out, cudaStream_t st)
@@ -462,17 +455,22 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gather(const float4* __restrict__ pos, int n,
                                                      const float* __restrict__ psi, GridArgs g,
                                                      float4* __restrict__ far4, double* __restrict__ partial,
-                                                     int* __restrict__ status)
+                                                     unsigned int* __restrict__ counter,
+                                                     double* __restrict__ psi_mean, int* __restrict__ status)
 {
     constexpr int H = P / 2;
     constexpr int NC = (P + 3) / 4;
-    __shared__ double red[kWarps][2];
+    __shared__ double red[kWarps];
+    __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, u = lane & 3;
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
     const long long plane = (long long)n0 * n1;
-    CSum qf, qq;                                           // sums of q phi_far, q^2
-    const float phi_dc = (float)(*g.psi_mean) * g.wsum;    // potential of psi's rounding-level k = 0 mode
+    // psi's mean (its rounding-level k = 0 mode): this CTA's share of the grid sum first
+    CSum ps;
+    const long long G = plane * n2;
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < G; i += (long long)gridDim.x * kThreads)
+        ps.add(psi[i]);
     for (int s0 = blockIdx.x * kGatherAtoms + warp * 8; s0 < n; s0 += gridDim.x * kGatherAtoms) {
         const int s = s0 + quad;
         const bool have = s < n;
@@ -545,25 +543,36 @@ __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gat
             ay += __shfl_xor_sync(0xffffffffu, ay, o);
             az += __shfl_xor_sync(0xffffffffu, az, o);
         }
-        aphi -= phi_dc;
         if (have && u == 0 && USR_IN_BOUNDS(s, g.max_atoms, status)) {
             const float qi = p.w;
             far4[s] = make_float4(-qi * ax, -qi * ay, -qi * az, aphi);
-            qf.add_product(qi, aphi);
-            qq.add_product(qi, qi);
         }
     }
-    // per-warp sums in a fixed order (lanes 0, 4, ..., 28 hold atoms), then per block: E_far, E_self
-    double e_far = warp_sum_d(0.5 * qf.value()), e_self = warp_sum_d(-0.5 * g.F0d * qq.value());
-    if (lane == 0) {
-        red[warp][0] = e_far;
-        red[warp][1] = e_self;
+    // psi's grid sum over all CTAs in a fixed order (the last CTA), then its mean
+    const double t = warp_sum_d(ps.value());
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += red[w];
+        partial[blockIdx.x] = v;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (threadIdx.x < 2) {
+    if (!is_last) return;
+    __threadfence();
+    double a = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) a += ((volatile double*)partial)[k];
+    a = warp_sum_d(a);
+    __syncthreads();
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * 2 + threadIdx.x] = v;
+        for (int w = 0; w < kWarps; ++w) v += red[w];
+        *psi_mean = v / (double)G;
+        *counter = 0u;
     }
 }
 
@@ -577,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gat
 __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __restrict__ pos,
                                                       const int* __restrict__ perm,
                                                       const unsigned long long* __restrict__ near_acc,
-                                                      const float4* __restrict__ far4, float F0, int nfar,
-                                                      const double* __restrict__ far_partial,
+                                                      const float4* __restrict__ far4, float F0, double F0d,
+                                                      float wsum, const double* __restrict__ psi_mean,
                                                       float4* __restrict__ out, float4* __restrict__ near_dbg,
                                                       float4* __restrict__ far_dbg, double* __restrict__ partial,
                                                       unsigned int* __restrict__ counter,
@@ -588,51 +597,53 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __res
     __shared__ double red[kWarps][3];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    CSum qn;
+    const float phi_dc = (float)(*psi_mean) * wsum;   // potential of psi's rounding-level k = 0 mode
+    CSum qn, qf, qq;                                  // sums of q phi_near, q phi_far, q^2
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < n; s += gridDim.x * kThreads) {
         const float4 nr = near_part(near_acc, s), f = far4[s];
         const float qi = pos[s].w;
+        const float phi_far = f.w - phi_dc;
         const int i = perm[s];
-        if (!USR_IN_BOUNDS(i, max_atoms, status)) continue;
-        out[i] = make_float4(nr.x + f.x, nr.y + f.y, nr.z + f.z, nr.w + f.w - F0 * qi);
-        if (near_dbg) near_dbg[i] = nr;
-        if (far_dbg) far_dbg[i] = f;
         qn.add_product(qi, nr.w);
+        qf.add_product(qi, phi_far);
+        qq.add_product(qi, qi);
+        if (!USR_IN_BOUNDS(i, max_atoms, status)) continue;
+        out[i] = make_float4(nr.x + f.x, nr.y + f.y, nr.z + f.z, nr.w + phi_far - F0 * qi);
+        if (near_dbg) near_dbg[i] = nr;
+        if (far_dbg) far_dbg[i] = make_float4(f.x, f.y, f.z, phi_far);
     }
-    const double e_near = warp_sum_d(0.5 * qn.value());
-    if (lane == 0) red[warp][0] = e_near;
+    double e[3] = {warp_sum_d(0.5 * qn.value()), warp_sum_d(0.5 * qf.value()), warp_sum_d(-0.5 * F0d * qq.value())};
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) red[warp][c] = e[c];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 3) {
         double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w][0];
-        partial[blockIdx.x] = v;
+        for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
+        partial[(size_t)blockIdx.x * 3 + threadIdx.x] = v;
         __threadfence();
-        const unsigned int ticket = atomicAdd(counter, 1u);
-        is_last = (ticket == gridDim.x - 1);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
+    // the last CTA: the three sums over all CTAs in a fixed order
     __threadfence();
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) acc[0] += ((volatile double*)partial)[k];
-    for (int k = threadIdx.x; k < nfar; k += kThreads) {
-        acc[1] += far_partial[(size_t)k * 2];
-        acc[2] += far_partial[(size_t)k * 2 + 1];
-    }
-    #pragma unroll
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads)
+        for (int c = 0; c < 3; ++c) acc[c] += ((volatile double*)partial)[(size_t)k * 3 + c];
     for (int c = 0; c < 3; ++c) acc[c] = warp_sum_d(acc[c]);
     __syncthreads();
     if (lane == 0)
         for (int c = 0; c < 3; ++c) red[warp][c] = acc[c];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double e[3] = {0.0, 0.0, 0.0};
+        double v[3] = {0.0, 0.0, 0.0};
         for (int w = 0; w < kWarps; ++w)
-            for (int c = 0; c < 3; ++c) e[c] += red[w][c];
-        energy[0] = e[0] + e[1] + e[2];
-        energy[1] = e[0];
-        energy[2] = e[1];
-        energy[3] = e[2];
+            for (int c = 0; c < 3; ++c) v[c] += red[w][c];
+        energy[0] = v[0] + v[1] + v[2];
+        energy[1] = v[0];
+        energy[2] = v[1];
+        energy[3] = v[2];
         *counter = 0u;
     }
 }
@@ -691,13 +702,13 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
 
 #define USR_GATHER_CASE(PP)                                                                \
     case PP:                                                                               \
-        k_gather<PP><<<nb, kThreads, 0, st>>>(spos, n, psi, g, far4, partial, status);     \
+        k_gather<PP><<<nb, kThreads, 0, st>>>(spos, n, psi, g, far4, partial, counter, psi_mean, status); \
         break;
 
-int gather_blocks(int n) { return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms)); }
+static int gather_blocks(int n) { return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms)); }
 
 void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
-                   double* partial, int* status, cudaStream_t st)
+                   double* partial, unsigned int* counter, double* psi_mean, int* status, cudaStream_t st)
 {
     const int nb = gather_blocks(n);
     switch (P) {
@@ -711,13 +722,13 @@ void launch_gather(int P, int n, const float4* spos, const float* psi, const Gri
 }
 
 void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
-                    const float4* far4, float F0, int nfar, const double* far_partial, float4* out,
+                    const float4* far4, const GridArgs& g, float4* out,
                     float4* near_dbg, float4* far_dbg, double* partial, unsigned int* counter, double* energy,
-                    int max_atoms, int* status, cudaStream_t st)
+                    int* status, cudaStream_t st)
 {
     const int nb = std::max(1, std::min(kCombineBlocks, (n + kThreads - 1) / kThreads));
-    k_combine<<<nb, kThreads, 0, st>>>(n, spos, perm, near_acc, far4, F0, nfar, far_partial, out, near_dbg, far_dbg,
-                                       partial, counter, energy, max_atoms, status);
+    k_combine<<<nb, kThreads, 0, st>>>(n, spos, perm, near_acc, far4, g.F0, g.F0d, g.wsum, g.psi_mean, out,
+                                       near_dbg, far_dbg, partial, counter, energy, g.max_atoms, status);
 }
 
 }  // namespace usr

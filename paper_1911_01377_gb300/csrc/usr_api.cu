@@ -69,7 +69,7 @@ struct usr_ctx {
     float *d_Bx = nullptr, *d_Ay = nullptr, *d_Az = nullptr, *d_wx = nullptr, *d_wy = nullptr, *d_wz = nullptr;
     double *d_spread_partial = nullptr, *d_mean = nullptr, *d_gather_partial = nullptr, *d_energy = nullptr;
     unsigned int* d_counters = nullptr;
-    double *d_psi_partial = nullptr, *d_psi_mean = nullptr;
+    double* d_psi_mean = nullptr;
     // spreading tiles and the per-axis tile tables
     float* d_tilebuf = nullptr;
     int* d_tab[3] = {nullptr, nullptr, nullptr};
@@ -142,7 +142,7 @@ void free_all(usr_ctx* c)
                     c->d_wpos, c->d_spos, c->d_nacc, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
                     c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_far4, c->d_tilebuf,
-                    c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_psi_partial, c->d_psi_mean, c->d_ktab};
+                    c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (TcConv* t : {&c->tcf, &c->tcc}) {
@@ -270,8 +270,7 @@ double usr::plan_device_bytes(const Plan& P)
     b += na * (4 * 4 + 16 * 7 + 32);                                               // per-atom arrays
     const double ngr = near_max_groups((int)na, (int)ncell);
     b += 8 * (ncell + 1) + 4 * ngr + 4;                                            // pair-kernel groups
-    b += 4 * G + 8 * (nsb + 2 * kGatherBlocks + kCombineBlocks) + 8 * 8 + 8 * kGridMeanBlocks +
-         4 * nsb * tile_floats(P.tile);
+    b += 4 * G + 8 * (nsb + kGatherBlocks + 3 * kCombineBlocks) + 8 * 10 + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
     if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
@@ -443,11 +442,10 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_psi, fl * G);
     ENSURE(c->d_spread_partial, db * nsb);
     ENSURE(c->d_mean, db);
-    ENSURE(c->d_gather_partial, db * (2 * usr::kGatherBlocks + usr::kCombineBlocks));
+    ENSURE(c->d_gather_partial, db * (usr::kGatherBlocks + 3 * usr::kCombineBlocks));
     ENSURE(c->d_far4, f4 * na);
     ENSURE(c->d_energy, db * 4);
-    ENSURE(c->d_counters, sizeof(unsigned int) * 4);
-    ENSURE(c->d_psi_partial, db * usr::kGridMeanBlocks);
+    ENSURE(c->d_counters, sizeof(unsigned int) * 8);
     ENSURE(c->d_psi_mean, db);
     ENSURE(c->d_in, f4 * na);
     ENSURE(c->d_out, f4 * na);
@@ -835,7 +833,7 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     }
     // stage boundaries: on the caller's stream 0 start, 1 cell list done, 2 pair kernel done, 9 the
     // combination may start (the far chain joined), 10 end; on the side stream 3 start, 4 spread done, 5-7
-    // passes x, y, z done, 8 psi mean done, 11 far gather done
+    // passes x, y, z done, 8 multilevel coarse steps done, 11 far gather done
     auto mark = [&](int k, cudaStream_t s) {
         if (c->prof == 1 || (c->prof == 2 && (k == 1 || k == 2))) cudaEventRecord(c->ev[k], s);
     };
@@ -894,9 +892,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
             }
             usr::launch_ml_prolong(c->ml, pc, t1, t2, c->d_psi, c->d_status, sd);
         }
-        usr::launch_grid_mean(c->grid, c->d_psi, c->d_psi_partial, c->d_counters + 2, c->d_psi_mean, sd);
         mark(8, sd);
-        usr::launch_gather(P.P, n, c->d_spos, c->d_psi, c->grid, c->d_far4, c->d_gather_partial, c->d_status, sd);
+        usr::launch_gather(P.P, n, c->d_spos, c->d_psi, c->grid, c->d_far4, c->d_gather_partial, c->d_counters + 4,
+                           c->d_psi_mean, c->d_status, sd);
         mark(11, sd);
         if (cudaEventRecord(c->ev_join, sd) != cudaSuccess) return USR_ERR_CUDA;
     }
@@ -911,11 +909,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     mark(9, st);
     {
         NvtxRange r("usr: near + far, energy");
-        const int nfar = usr::gather_blocks(n);
-        usr::launch_combine(n, c->d_spos, c->d_perm, c->d_nacc, c->d_far4, c->grid.F0, nfar, c->d_gather_partial,
-                            out, c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
-                            c->d_gather_partial + 2 * (size_t)nfar, c->d_counters + 1, en, c->max_atoms,
-                            c->d_status, st);
+        usr::launch_combine(n, c->d_spos, c->d_perm, c->d_nacc, c->d_far4, c->grid, out,
+                            c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
+                            c->d_gather_partial + usr::kGatherBlocks, c->d_counters + 1, en, c->d_status, st);
         mark(10, st);
     }
     if (c->vir) {
@@ -970,7 +966,7 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
         (s = usr::conv_tc_setup(true, usr::kConvTcMaxSmem)) != USR_OK)
         return fail(s);
     if ((s = configure(c, p, 0)) != USR_OK) return fail(s);
-    if (cudaMemset(c->d_counters, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
+    if (cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess)
         return fail(USR_ERR_CUDA);
@@ -1175,9 +1171,9 @@ extern "C" usr_status usr_stage_times(usr_ctx* c, float* ms)
         return cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]) == cudaSuccess ? USR_OK : USR_ERR_CUDA;
     }
     if (cudaEventSynchronize(c->ev[10]) != cudaSuccess) return USR_ERR_CUDA;
-    // (from, to) event pairs of the stages; the gather stage adds the psi mean and the far gather (11 - 7)
-    // to the combination (10 - 9); the wait for the later of the two branches (between 2 or 11 and 9) is in
-    // no stage
+    // (from, to) event pairs of the stages; the gather stage adds the multilevel coarse steps (if any) and
+    // the far gather with psi's mean (11 - 7) to the combination (10 - 9); the wait for the later of the two
+    // branches (between 2 or 11 and 9) is in no stage
     static const int from[USR_NSTAGES] = {0, 1, 3, 4, 5, 6, 9}, to[USR_NSTAGES] = {1, 2, 4, 5, 6, 7, 10};
     for (int k = 0; k < USR_NSTAGES; ++k) {
         float t = 0.f;

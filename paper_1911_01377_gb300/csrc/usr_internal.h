@@ -283,20 +283,15 @@ usr_status make_tmap(CUtensorMap* m, const void* ptr, bool bf16, long long rows,
 size_t conv_tc_smem(const ConvTcArgs& g);
 usr_status conv_tc_setup(bool bf16, size_t smem);
 void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int batches, cudaStream_t st);
-void launch_grid_mean(const GridArgs& g, const float* psi, double* partial, unsigned int* counter, double* mean,
-                      cudaStream_t st);
-/* far part at each of the n sorted atoms into far4 (F_far, phi_far), per CTA b the E_far and E_self sums into
-   partial[2 b], partial[2 b + 1]; gather_blocks(n) CTAs (kGatherBlocks at most) */
+/* far part at each of the n sorted atoms into far4 (-q grad phi, phi before the k = 0 correction), and psi's
+   grid mean into psi_mean through per-CTA sums in partial (kGatherBlocks CTAs at most) and the last CTA */
 void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
-                   double* partial, int* status, cudaStream_t st);
-int gather_blocks(int n);
+                   double* partial, unsigned int* counter, double* psi_mean, int* status, cudaStream_t st);
 /* near + far in caller order into out (and the parts into near_dbg / far_dbg when non-null); energy[0..3] =
-   total, near, far, self from the per-block E_near sums (partial, kCombineBlocks at most) and the gather's
-   nfar block pairs */
+   total, near, far, self through per-CTA sums in partial (3 per CTA, kCombineBlocks CTAs at most) */
 void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
-                    const float4* far4, float F0, int nfar, const double* far_partial, float4* out,
-                    float4* near_dbg, float4* far_dbg, double* partial, unsigned int* counter, double* energy,
-                    int max_atoms, int* status, cudaStream_t st);
+                    const float4* far4, const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg,
+                    double* partial, unsigned int* counter, double* energy, int* status, cudaStream_t st);
 int tile_blocks(const TileGeom& tg);
 size_t tile_floats(const TileGeom& tg);
 usr_status grid_kernel_setup(size_t smem_bytes);
