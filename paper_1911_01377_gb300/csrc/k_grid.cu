@@ -450,17 +450,18 @@ __device__ __forceinline__ float4 near_part(const unsigned long long* __restrict
 #ifndef USR_GATHER_MINB
 #define USR_GATHER_MINB 2   // CTAs per SM the 8- and 10-point gathers are compiled for (3 spills; measured slower)
 #endif
+constexpr int kGThreads = USR_GATHER_THREADS;   // gather CTA size
+constexpr int kGWarps = kGThreads / 32;
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gather(const float4* __restrict__ pos, int n,
-                                                     const float* __restrict__ psi, GridArgs g,
-                                                     float4* __restrict__ far4, double* __restrict__ partial,
-                                                     unsigned int* __restrict__ counter,
-                                                     double* __restrict__ psi_mean, int* __restrict__ status)
+__global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 256 / kGThreads)
+    k_gather(const float4* __restrict__ pos, int n, const float* __restrict__ psi, GridArgs g,
+             float4* __restrict__ far4, double* __restrict__ partial, unsigned int* __restrict__ counter,
+             double* __restrict__ psi_mean, int* __restrict__ status)
 {
     constexpr int H = P / 2;
     constexpr int NC = (P + 3) / 4;
-    __shared__ double red[kWarps];
+    __shared__ double red[kGWarps];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, u = lane & 3;
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gat
     // psi's mean (its rounding-level k = 0 mode): this CTA's share of the grid sum first
     CSum ps;
     const long long G = plane * n2;
-    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < G; i += (long long)gridDim.x * kThreads)
+    for (long long i = (long long)blockIdx.x * kGThreads + threadIdx.x; i < G; i += (long long)gridDim.x * kGThreads)
         ps.add(psi[i]);
     for (int s0 = blockIdx.x * kGatherAtoms + warp * 8; s0 < n; s0 += gridDim.x * kGatherAtoms) {
         const int s = s0 + quad;
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gat
     __syncthreads();
     if (threadIdx.x == 0) {
         double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w];
+        for (int w = 0; w < kGWarps; ++w) v += red[w];
         partial[blockIdx.x] = v;
         __threadfence();
         is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
@@ -563,14 +564,14 @@ __global__ void __launch_bounds__(kThreads, P <= 10 ? USR_GATHER_MINB : 2) k_gat
     if (!is_last) return;
     __threadfence();
     double a = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads) a += ((volatile double*)partial)[k];
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kGThreads) a += ((volatile double*)partial)[k];
     a = warp_sum_d(a);
     __syncthreads();
     if (lane == 0) red[warp] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
         double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w];
+        for (int w = 0; w < kGWarps; ++w) v += red[w];
         *psi_mean = v / (double)G;
         *counter = 0u;
     }
@@ -702,10 +703,13 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
 
 #define USR_GATHER_CASE(PP)                                                                \
     case PP:                                                                               \
-        k_gather<PP><<<nb, kThreads, 0, st>>>(spos, n, psi, g, far4, partial, counter, psi_mean, status); \
+        k_gather<PP><<<nb, kGThreads, 0, st>>>(spos, n, psi, g, far4, partial, counter, psi_mean, status); \
         break;
 
-static int gather_blocks(int n) { return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms)); }
+static int gather_blocks(int n)
+{
+    return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms));
+}
 
 void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
                    double* partial, unsigned int* counter, double* psi_mean, int* status, cudaStream_t st)

@@ -34,6 +34,13 @@ struct NvtxRange {
 
 /* One tensor-core convolution (three passes): split operands (hi, lo), B tables and tensor maps per pass, the
    per-term means of the x and y kernels. */
+#ifndef USR_SIDE_PRIORITY
+#define USR_SIDE_PRIORITY 0   // priority of the far chain's stream: 0 highest, 1 default, 2 lowest
+#endif
+#ifndef USR_NEAR_CTAS
+#define USR_NEAR_CTAS 4   // one CTA slot per SM left to the far chain (measured: 5 and 3 slower)
+#endif
+
 struct TcConv {
     bool bf16 = false;
     void *rho_hi = nullptr, *rho_lo = nullptr, *X_hi = nullptr, *X_lo = nullptr, *Y_hi = nullptr, *Y_lo = nullptr;
@@ -105,7 +112,7 @@ struct usr_ctx {
     float4* d_far4 = nullptr;      // far part per sorted atom (gather -> combination)
     bool keep_parts = false;
     bool inject_timeout = false;
-    int near_ctas_per_sm = 0;      // persistent pair-kernel CTAs per SM (0: as many as fit)   // the next evaluation's first tensor-core pass waits on a barrier nothing completes
+    int near_ctas_per_sm = USR_NEAR_CTAS;   // persistent pair-kernel CTAs per SM (0: as many as fit)
     bool parts_valid = false;
     // the far chain (spread, convolutions, psi mean) runs on `side`, a high-priority stream forked from and
     // joined back to the caller's stream, while the pair kernel runs on the caller's stream
@@ -975,7 +982,9 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     {
         int least = 0, greatest = 0;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking,
+                                         USR_SIDE_PRIORITY == 0 ? greatest : (USR_SIDE_PRIORITY == 1 ? 0 : least))
+                != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
             return fail(USR_ERR_CUDA);

@@ -22,8 +22,11 @@ constexpr int kMlT = 16;           // multilevel transfer half-width in fine poi
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
-constexpr int kGatherAtoms = 64;       // atoms per gather CTA pass (8 warps x 8 quads)
-constexpr int kGatherBlocks = 1216;    // gather CTAs at most (eight per SM)
+#ifndef USR_GATHER_THREADS
+#define USR_GATHER_THREADS 128
+#endif
+constexpr int kGatherAtoms = USR_GATHER_THREADS / 4;       // atoms per gather CTA pass (a quad of lanes each)
+constexpr int kGatherBlocks = 8 * 152 * 256 / USR_GATHER_THREADS;   // gather CTAs at most
 
 /*
  * Cell blocks of the spreading / interpolation kernels and their smem tiles.
