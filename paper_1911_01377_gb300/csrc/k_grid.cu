@@ -69,6 +69,19 @@ struct CSum {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+/* A compensated sum over the warp (xor butterfly, FP32 with the error terms carried), as FP64: one conversion
+   per warp instead of five FP64 additions per thread (GB300's FP64 pipe is narrow). Callers use lane 0's value. */
+__device__ __forceinline__ double warp_sum_c(CSum cs)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s = __shfl_xor_sync(0xffffffffu, cs.s, o), c = __shfl_xor_sync(0xffffffffu, cs.c, o);
+        cs.add(s);
+        cs.c = __fadd_rn(cs.c, c);
+    }
+    return cs.value();
+}
+
 __device__ __forceinline__ float warp_sum_f(float v)
 {
     #pragma unroll
@@ -261,9 +274,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
             cs.add(v.z);
             cs.add(v.w);
         }
-        local = cs.value();
+        local = warp_sum_c(cs);
     }
-    local = warp_sum_d(local);
     if (lane == 0) red[warp] = local;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(256) k_grid_mean(long long G, const float* __r
             cs.add_product(psi[i], w[i]);
         else
             cs.add(psi[i]);
-    double s = warp_sum_d(cs.value());
+    double s = warp_sum_c(cs);
     if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -550,7 +562,7 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
         }
     }
     // psi's grid sum over all CTAs in a fixed order (the last CTA), then its mean
-    const double t = warp_sum_d(ps.value());
+    const double t = warp_sum_c(ps);
     if (lane == 0) red[warp] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -613,7 +625,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __res
         if (near_dbg) near_dbg[i] = nr;
         if (far_dbg) far_dbg[i] = make_float4(f.x, f.y, f.z, phi_far);
     }
-    double e[3] = {warp_sum_d(0.5 * qn.value()), warp_sum_d(0.5 * qf.value()), warp_sum_d(-0.5 * F0d * qq.value())};
+    double e[3] = {0.5 * warp_sum_c(qn), 0.5 * warp_sum_c(qf), -0.5 * F0d * warp_sum_c(qq)};
     if (lane == 0)
         for (int c = 0; c < 3; ++c) red[warp][c] = e[c];
     __syncthreads();

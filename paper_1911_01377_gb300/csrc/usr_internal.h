@@ -26,7 +26,10 @@ constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at 
 #define USR_GATHER_THREADS 128
 #endif
 constexpr int kGatherAtoms = USR_GATHER_THREADS / 4;       // atoms per gather CTA pass (a quad of lanes each)
-constexpr int kGatherBlocks = 8 * 152 * 256 / USR_GATHER_THREADS;   // gather CTAs at most
+#ifndef USR_GATHER_BLOCKS
+#define USR_GATHER_BLOCKS (8 * 152)   // measured: 4 x 152 slower at 1 M charges, 16 x 152 slower on the slab
+#endif
+constexpr int kGatherBlocks = USR_GATHER_BLOCKS;   // gather CTAs at most
 
 /*
  * Cell blocks of the spreading / interpolation kernels and their smem tiles.
