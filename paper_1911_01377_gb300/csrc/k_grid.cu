@@ -315,11 +315,12 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
                                                      void* __restrict__ rho_lo, float* __restrict__ rho32,
                                                      int* __restrict__ status)
 {
-    const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
-    const long long G = (long long)n0 * n1 * n2;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= G) return;
-    const int x = (int)(idx % n0), y = (int)((idx / n0) % n1), z = (int)(idx / ((long long)n0 * n1));
+    // grid: x over the (y, x) plane in blocks of 256, y over z (32-bit index arithmetic)
+    const int n0 = g.box.n[0], n1 = g.box.n[1];
+    const int pxy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pxy >= n0 * n1) return;
+    const int y = pxy / n0, x = pxy - y * n0, z = blockIdx.y;
+    const long long idx = (long long)z * n0 * n1 + pxy;
     const int T0 = g.tg.T[0], T1 = g.tg.T[1], T2 = g.tg.T[2];
     const long long TT = (long long)T0 * T1 * T2;
     const int nb0 = g.tg.nbk[0], nb1 = g.tg.nbk[1];
@@ -703,8 +704,7 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
         default:
         USR_SPREAD_CASE(16)
     }
-    const long long G = (long long)g.box.n[0] * g.box.n[1] * g.box.n[2];
-    const unsigned nr = (unsigned)((G + 255) / 256);
+    const dim3 nr((unsigned)((g.box.n[0] * g.box.n[1] + 255) / 256), (unsigned)g.box.n[2]);
     if (split == 1)
         k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32, status);
     else if (split == 2)

@@ -34,6 +34,9 @@ struct NvtxRange {
 
 /* One tensor-core convolution (three passes): split operands (hi, lo), B tables and tensor maps per pass, the
    per-term means of the x and y kernels. */
+#ifndef USR_TC_MIN_CTAS
+#define USR_TC_MIN_CTAS 0     // split a tensor-core pass into more N tiles below this many CTAs
+#endif
 #ifndef USR_SIDE_PRIORITY
 #define USR_SIDE_PRIORITY 0   // priority of the far chain's stream: 0 highest, 1 default, 2 lowest
 #endif
@@ -202,12 +205,17 @@ size_t tab_ints(const Plan& P, int a)
     return head + P.red_pair[a].size();
 }
 
-/* Tile shape of one tensor-core pass with n_out output columns and contraction K. */
-void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16)
+/*
+ * Tile shape of one tensor-core pass with n_out output columns and contraction K, over `ctas_m` M tiles (lines /
+ * 128 x batches).  When that gives fewer than USR_TC_MIN_CTAS CTAs, the columns are split into more N tiles (16
+ * columns at least) so that more SMs share the pass.
+ */
+void tc_shape(usr::ConvTcArgs& a, int n_out, int K, bool bf16, long long ctas_m)
 {
     a.n_out = n_out;
     a.K = K;
     a.ntiles = (n_out + 1 + 255) / 256;
+    while (ctas_m * a.ntiles < USR_TC_MIN_CTAS && (n_out + a.ntiles) / (a.ntiles + 1) >= 16) ++a.ntiles;
     a.cols = (n_out + a.ntiles - 1) / a.ntiles;
     a.NT = ((a.cols + 1 + 15) / 16) * 16;
     a.tmem_cols = 32;
@@ -345,7 +353,7 @@ usr_status setup_tc(usr_ctx* c, TcConv& t, bool bf, int N, int nx, int ny, int n
     for (int ps = 0; ps < 3; ++ps) {
         usr::ConvTcArgs& a = t.targs[ps];
         std::memset(&a, 0, sizeof(a));
-        tc_shape(a, n_out[ps], Ks[ps], bf);
+        tc_shape(a, n_out[ps], Ks[ps], bf, (long long)((lines[ps] + 127) / 128) * batches[ps]);
         const size_t nB = (size_t)batches[ps] * a.ntiles * a.NT * a.K;
         if ((s = ensure(c, &t.Bt_hi[ps], es * nB)) != USR_OK || (s = ensure(c, &t.Bt_lo[ps], es * nB)) != USR_OK)
             return s;
