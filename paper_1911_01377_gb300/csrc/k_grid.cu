@@ -18,12 +18,12 @@
  *   reduce   one thread per grid point adds the tiles that hold it, in block
  *            order, and subtracts the grid mean.
  *   gather   phi_far,i = sum_g w(g - r_i) psi_g and F_far,i = -q_i grad phi_far,i
- *            (the second spreading Gaussian of Eq. 32's 1/|S(k)|^2).  The CTA
- *            stages its psi tile in shared memory; a quad of lanes per atom
- *            contracts the stencil separably (z first, per (x, y) column), adds
- *            the near part and the self term -F(0) q_i, writes (F, phi) in
- *            caller order and reduces E = 1/2 sum q_i phi_i and its parts
- *            (compensated FP32 within a thread, FP64 across threads and blocks).
+ *            (the second spreading Gaussian of Eq. 32's 1/|S(k)|^2), per sorted
+ *            atom, reading psi from global memory; contracts the stencil
+ *            separably (z first, per (x, y) column); also psi's grid mean.
+ *   combine  after the pair kernel: near + far + the self term -F(0) q_i in
+ *            caller order, and E = 1/2 sum q_i phi_i and its parts
+ *            (compensated FP32 within a warp, FP64 across warps and blocks).
  */
 #include <cuda_bf16.h>
 
@@ -456,15 +456,20 @@ __device__ __forceinline__ float4 near_part(const unsigned long long* __restrict
 /*
  * Far part at every sorted atom (the gather of Sec. V: the spreading Gaussian of the atom against psi,
  * and its gradient), read straight from psi in global memory: consecutive sorted atoms are neighbours in
- * space, so a CTA's stencils overlap and hit in L1 / L2.  A CTA takes kGatherAtoms consecutive atoms per
- * pass, a quad of lanes per atom: lane u of the quad takes the stencil columns x = u, u + 4, ... of every
- * row, contracting z first.  Writes far4[s] = (-q grad phi, phi_far) and per CTA the E_far, E_self sums.
+ * space, so a CTA's stencils overlap and hit in L1 / L2.  A CTA takes consecutive atoms, gather_lanes(P)
+ * lanes per atom: lane u takes the stencil columns x = u, u + lanes, ... of every row, contracting z first,
+ * so the lanes of an atom read one contiguous run of a row per load.  Writes far4[s] = (-q grad phi, phi
+ * before the k = 0 correction); the CTAs also sum psi, and the last one writes its mean.
  */
 #ifndef USR_GATHER_MINB
 #define USR_GATHER_MINB 2   // CTAs per SM the 8- and 10-point gathers are compiled for (3 spills; measured slower)
 #endif
 constexpr int kGThreads = USR_GATHER_THREADS;   // gather CTA size
 constexpr int kGWarps = kGThreads / 32;
+#ifndef USR_GATHER_LANES
+#define USR_GATHER_LANES 4   // lanes per atom (8 or 16, one stencil column per lane: measured no faster)
+#endif
+__host__ __device__ constexpr int gather_lanes(int) { return USR_GATHER_LANES; }
 
 template <int P>
 __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 256 / kGThreads)
@@ -473,11 +478,14 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
              double* __restrict__ psi_mean, int* __restrict__ status)
 {
     constexpr int H = P / 2;
-    constexpr int NC = (P + 3) / 4;
+    constexpr int LPA = gather_lanes(P);       // lanes per atom
+    constexpr int NC = (P + LPA - 1) / LPA;    // stencil columns per lane
+    constexpr int APW = 32 / LPA;              // atoms per warp pass
+    constexpr int APC = kGWarps * APW;         // atoms per CTA pass
     __shared__ double red[kGWarps];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int quad = lane >> 2, u = lane & 3;
+    const int slot = lane / LPA, u = lane % LPA;
     const int n0 = g.box.n[0], n1 = g.box.n[1], n2 = g.box.n[2];
     const long long plane = (long long)n0 * n1;
     // psi's mean (its rounding-level k = 0 mode): this CTA's share of the grid sum first
@@ -485,8 +493,8 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
     const long long G = plane * n2;
     for (long long i = (long long)blockIdx.x * kGThreads + threadIdx.x; i < G; i += (long long)gridDim.x * kGThreads)
         ps.add(psi[i]);
-    for (int s0 = blockIdx.x * kGatherAtoms + warp * 8; s0 < n; s0 += gridDim.x * kGatherAtoms) {
-        const int s = s0 + quad;
+    for (int s0 = blockIdx.x * APC + warp * APW; s0 < n; s0 += gridDim.x * APC) {
+        const int s = s0 + slot;
         const bool have = s < n;
         const float4 p = pos[have ? s : s0];
         const float pc[3] = {p.x, p.y, p.z};
@@ -510,7 +518,7 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
         }
         #pragma unroll
         for (int m = 0; m < NC; ++m) {
-            const int c = u + 4 * m;
+            const int c = u + LPA * m;
             const float d0 = (float)(c - H + 1) - tt[0];
             wx[m] = c < P ? __expf(-d0 * d0 * g.hh[0]) : 0.f;
             dx[m] = wx[m] * d0 * g.dfac[0];
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
             float r0 = 0.f, r1 = 0.f, r2 = 0.f;
             #pragma unroll
             for (int m = 0; m < NC; ++m) {
-                if (u + 4 * m >= P) continue;
+                if (u + LPA * m >= P) continue;
                 const float* col = psi + yo + xo[m];
                 float v[P];
                 #pragma unroll
@@ -549,9 +557,9 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
             ay = fmaf(dy, r0, ay);
             az = fmaf(wy, r2, az);
         }
-        // the four lanes of a quad hold disjoint partial sums
+        // the lanes of an atom hold disjoint partial sums
         #pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
+        for (int o = 1; o < LPA; o <<= 1) {
             aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
             ax += __shfl_xor_sync(0xffffffffu, ax, o);
             ay += __shfl_xor_sync(0xffffffffu, ay, o);
@@ -718,15 +726,16 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
         k_gather<PP><<<nb, kGThreads, 0, st>>>(spos, n, psi, g, far4, partial, counter, psi_mean, status); \
         break;
 
-static int gather_blocks(int n)
+static int gather_blocks(int n, int P)
 {
-    return std::max(1, std::min(kGatherBlocks, (n + kGatherAtoms - 1) / kGatherAtoms));
+    const int apc = kGThreads / gather_lanes(P);   // atoms per CTA pass
+    return std::max(1, std::min(kGatherBlocks, (n + apc - 1) / apc));
 }
 
 void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
                    double* partial, unsigned int* counter, double* psi_mean, int* status, cudaStream_t st)
 {
-    const int nb = gather_blocks(n);
+    const int nb = gather_blocks(n, P);
     switch (P) {
         USR_GATHER_CASE(8)
         USR_GATHER_CASE(10)

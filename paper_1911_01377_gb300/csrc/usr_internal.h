@@ -25,7 +25,6 @@ constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at 
 #ifndef USR_GATHER_THREADS
 #define USR_GATHER_THREADS 128
 #endif
-constexpr int kGatherAtoms = USR_GATHER_THREADS / 4;       // atoms per gather CTA pass (a quad of lanes each)
 #ifndef USR_GATHER_BLOCKS
 #define USR_GATHER_BLOCKS (8 * 152)   // measured: 4 x 152 slower at 1 M charges, 16 x 152 slower on the slab
 #endif
