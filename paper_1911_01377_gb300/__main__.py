@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--spread-points", type=int, default=0)
     ap.add_argument("--spread-sigma", type=float, default=0.0, help="spreading width / grid spacing")
     ap.add_argument("--virial", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--multilevel", type=int, default=0, choices=[0, 1], help="wide terms on the coarse grid")
     args = ap.parse_args(argv)
 
     import torch
@@ -33,7 +34,8 @@ def main(argv=None):
     w = W.get(args.workload)
     r_c = args.rc or w.r_c[0]
     ctx = usr.USeries(w.box, w.grid, r_c, args.series, max_atoms=w.n, conv=args.conv,
-                      spread_points=args.spread_points, spread_sigma_over_h=args.spread_sigma, virial=args.virial)
+                      spread_points=args.spread_points, spread_sigma_over_h=args.spread_sigma, virial=args.virial,
+                      multilevel=args.multilevel)
     usr.usr_set_profiling(ctx.ctx, True)
     x = torch.from_numpy(w.xyzq).cuda()
     out = torch.empty((w.n, 4), dtype=torch.float32, device="cuda")
@@ -49,7 +51,8 @@ def main(argv=None):
         raise usr.UsrError(st, "usr_eval")
     e = en.cpu().tolist()
     info = ctx.info
-    print(f"{w.name}: n={w.n} r_c={r_c:g} grid={w.grid} terms={info.n_terms} cells={tuple(info.cells)}")
+    print(f"{w.name}: n={w.n} r_c={r_c:g} grid={w.grid} terms={info.n_terms} (coarse {info.n_terms_coarse}) "
+          f"cells={tuple(info.cells)}")
     print(f"E={e[0]:.10f} E_near={e[1]:.10f} E_far={e[2]:.10f} E_self={e[3]:.10f}")
     if args.virial:
         print("virial:", ctx.virial().cpu().numpy().round(6).tolist())
