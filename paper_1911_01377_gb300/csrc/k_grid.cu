@@ -467,9 +467,12 @@ __device__ __forceinline__ float4 near_part(const unsigned long long* __restrict
 constexpr int kGThreads = USR_GATHER_THREADS;   // gather CTA size
 constexpr int kGWarps = kGThreads / 32;
 #ifndef USR_GATHER_LANES
-#define USR_GATHER_LANES 4   // lanes per atom (8 or 16, one stencil column per lane: measured no faster)
+#define USR_GATHER_LANES 0   // lanes per atom; 0: 5 for P = 10 (two columns each), else 4
 #endif
-__host__ __device__ constexpr int gather_lanes(int) { return USR_GATHER_LANES; }
+__host__ __device__ constexpr int gather_lanes(int P)
+{
+    return USR_GATHER_LANES ? USR_GATHER_LANES : (P == 10 ? 5 : 4);
+}
 
 template <int P>
 __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 256 / kGThreads)
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
         ps.add(psi[i]);
     for (int s0 = blockIdx.x * APC + warp * APW; s0 < n; s0 += gridDim.x * APC) {
         const int s = s0 + slot;
-        const bool have = s < n;
+        const bool have = slot < APW && s < n;     // lanes past APW x LPA hold no atom
         const float4 p = pos[have ? s : s0];
         const float pc[3] = {p.x, p.y, p.z};
         int base[3];
@@ -557,13 +560,25 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
             ay = fmaf(dy, r0, ay);
             az = fmaf(wy, r2, az);
         }
-        // the lanes of an atom hold disjoint partial sums
-        #pragma unroll
-        for (int o = 1; o < LPA; o <<= 1) {
-            aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-            az += __shfl_xor_sync(0xffffffffu, az, o);
+        // the lanes of an atom hold disjoint partial sums: a butterfly for a power of two, else lane u = 0
+        // adds those of u = 1, 2, ... in order
+        if ((LPA & (LPA - 1)) == 0) {
+            #pragma unroll
+            for (int o = 1; o < LPA; o <<= 1) {
+                aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+            }
+        } else {
+            const float p0 = aphi, p1 = ax, p2 = ay, p3 = az;
+            #pragma unroll
+            for (int o = 1; o < LPA; ++o) {
+                aphi += __shfl_down_sync(0xffffffffu, p0, o);
+                ax += __shfl_down_sync(0xffffffffu, p1, o);
+                ay += __shfl_down_sync(0xffffffffu, p2, o);
+                az += __shfl_down_sync(0xffffffffu, p3, o);
+            }
         }
         if (have && u == 0 && USR_IN_BOUNDS(s, g.max_atoms, status)) {
             const float qi = p.w;
