@@ -366,9 +366,10 @@ def lattice_water_box(seed: int, n_charges: int, density: float = 0.1) -> Tuple[
 
 
 # The serving stream's evaluation form: TF32x3 tensor-core convolutions and a 10-point spreading stencil of
-# width 0.9 h.  On its ~1 A grids at r_c = 9 A the 8-point stencil (width 0.83 h) leaves about 1.2e-4 of the
-# far potential, and single-grid BF16x3 about 6e-4 (the wide terms' near-constant parts carry the operand
-# rounding of the 16-bit split); this form stays near 2e-5.
+# width 0.9 h.  On the stream's lattice-placed boxes (~1 A grids, r_c = 9 A) the grid errors of the ordered
+# charges add up coherently: the 8-point stencil (width 0.83 h) leaves about 1.2e-4 of the far potential and
+# single-grid BF16x3 about 6e-4 (the wide terms' near-constant parts carry the 16-bit split's rounding), against
+# 6-7e-5 for randomly placed waters; this form stays near 2e-5 on the lattice boxes.
 SERVING_FORM = dict(conv=1, spread_points=10, spread_sigma_over_h=0.9)
 
 
