@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
                                                    int* __restrict__ slot, float4* __restrict__ wpos,
                                                    int* __restrict__ status)
 {
+    pdl_trigger();   // dependents may be scheduled now; they wait for this grid in pdl_wait
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = xyzq[i];
@@ -70,10 +72,12 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
  * gfull[0..ncell], the one partial group a cell may end with into
  * gpart[0..ncell]; and the kernel's work-queue counter is set to zero.
  */
-__global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict__ count, int* __restrict__ start,
+__global__ void __launch_bounds__(1024) k_scan(int ncell, int* __restrict__ count, int* __restrict__ start,
                                                int* __restrict__ pstart, int* __restrict__ gfull,
                                                int* __restrict__ gpart, int gcl, int* __restrict__ queue)
 {
+    pdl_trigger();   // dependents may be scheduled now; they wait for this grid in pdl_wait
+    pdl_wait();
     __shared__ int4 warp_sums[32];
     __shared__ int4 carry;
     if (threadIdx.x == 0) {
@@ -85,6 +89,7 @@ __global__ void __launch_bounds__(1024) k_scan(int ncell, const int* __restrict_
     for (int base = 0; base < ncell; base += 1024) {
         const int i = base + threadIdx.x;
         const int v = i < ncell ? count[i] : 0;
+        if (i < ncell) count[i] = 0;   // ready for the next evaluation's counting
         const int vp = (v + 7) & ~7;
         const int vf = (vp >> 3) / gcl, vq = (vp >> 3) % gcl != 0 ? 1 : 0;
         int4 x = make_int4(v, vp, vf, vq);
@@ -136,6 +141,8 @@ __global__ void __launch_bounds__(256) k_place(int n, const int* __restrict__ ce
                                                const int* __restrict__ start, int* __restrict__ unsorted,
                                                int* __restrict__ status)
 {
+    pdl_trigger();   // dependents may be scheduled now; they wait for this grid in pdl_wait
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int d = start[cell_of[i]] + slot[i];
@@ -156,6 +163,8 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(int n, const int* __
                                                             const float4* __restrict__ wpos, int* __restrict__ perm,
                                                             float4* __restrict__ spos, int* __restrict__ status)
 {
+    pdl_trigger();   // dependents may be scheduled now; they wait for this grid in pdl_wait
+    pdl_wait();
     __shared__ int v[kSortMax];
     const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
@@ -238,6 +247,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cluster_build(const int* __res
                                                                 int max_slots, int max_groups,
                                                                 int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     __shared__ int ks[kSortMax];
     const int c = blockIdx.x;
     const int s0 = start[c], m = start[c + 1] - s0;
@@ -328,13 +338,14 @@ void launch_bin_sorted(int n, const float4* xyzq, const BoxF& b, int ncell, int*
                        float4* wpos, int* cell_start, int* pstart, int* gfull, int* gpart, int* queue, int* unsorted,
                        int* perm, float4* spos, int* status, cudaStream_t st)
 {
+    // count[] is zero on entry: the context zeroes it when it is (re)configured, and k_scan zeroes every
+    // entry after reading it, ready for the next evaluation (no memset between the kernels)
     const int gcl = near_group_clusters();
-    cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, st);
     int nb = (n + 255) / 256;
-    k_bin_count<<<nb, 256, 0, st>>>(n, xyzq, b, count, cell_of, slot, wpos, status);
-    k_scan<<<1, 1024, 0, st>>>(ncell, count, cell_start, pstart, gfull, gpart, gcl, queue);
-    k_place<<<nb, 256, 0, st>>>(n, cell_of, slot, cell_start, unsorted, status);
-    k_cell_sort<<<ncell, kSortThreads, 0, st>>>(n, cell_start, unsorted, wpos, perm, spos, status);
+    launch_pdl(k_bin_count, nb, 256, 0, st, n, xyzq, b, count, cell_of, slot, wpos, status);
+    launch_pdl(k_scan, 1, 1024, 0, st, ncell, count, cell_start, pstart, gfull, gpart, gcl, queue);
+    launch_pdl(k_place, nb, 256, 0, st, n, cell_of, slot, cell_start, unsorted, status);
+    launch_pdl(k_cell_sort, ncell, kSortThreads, 0, st, n, cell_start, unsorted, wpos, perm, spos, status);
 }
 
 /* The pair kernels' clusters from the sorted cell list (slot[] of launch_bin_sorted is reused for keys). */
@@ -343,9 +354,9 @@ void launch_clusters(int n, const BoxF& b, int ncell, const int* cell_start, con
                      int* ccell, float4* bblo, float4* bbhi, unsigned long long* near_acc, int max_clusters,
                      int max_groups, int* status, cudaStream_t st)
 {
-    k_cluster_build<<<ncell, kSortThreads, 0, st>>>(cell_start, pstart, gfull, gpart, near_group_clusters(), b, spos,
-                                                     key, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc, n,
-                                                     8 * max_clusters, max_groups, status);
+    launch_pdl(k_cluster_build, ncell, kSortThreads, 0, st, cell_start, pstart, gfull, gpart, near_group_clusters(),
+               b, spos, key, cpos, cidx, ccell, bblo, bbhi, gfirst, near_acc, n, 8 * max_clusters, max_groups,
+               status);
 }
 
 }  // namespace usr

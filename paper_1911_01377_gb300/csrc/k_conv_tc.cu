@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mB_hi,
                                                            const __grid_constant__ CUtensorMap mB_lo, ConvTcArgs g)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     constexpr int KMMA = BF16 ? 16 : 8;                // K of one MMA
     constexpr int KSTAGE = BF16 ? 64 : 32;             // K per 128-byte row
     constexpr int KSUB = KSTAGE / KMMA;                // MMAs per stage and operand pair (4)
@@ -412,9 +413,9 @@ void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int bat
     dim3 grid((g.lines + 127) / 128, batches, g.ntiles);
     const size_t smem = (size_t)g.smem;
     if (bf16)
-        k_conv_tc<true><<<grid, kTcThreads, smem, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, g);
+        launch_pdl(k_conv_tc<true>, grid, kTcThreads, smem, st, m.a_hi, m.a_lo, m.b_hi, m.b_lo, g);
     else
-        k_conv_tc<false><<<grid, kTcThreads, smem, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, g);
+        launch_pdl(k_conv_tc<false>, grid, kTcThreads, smem, st, m.a_hi, m.a_lo, m.b_hi, m.b_lo, g);
 }
 
 }  // namespace usr

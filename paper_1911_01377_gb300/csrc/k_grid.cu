@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
                                                         unsigned int* __restrict__ counter,
                                                         double* __restrict__ mean, int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     constexpr int H = P / 2;
     static_assert(P <= 2 * kWarps && P <= 32, "at most two stencil rows per warp");
     extern __shared__ float4 smem4[];
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(256) k_tile_reduce(GridArgs g, const float* __
                                                      void* __restrict__ rho_lo, float* __restrict__ rho32,
                                                      int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     // grid: x over the (y, x) plane in blocks of 256, y over z (32-bit index arithmetic)
     const int n0 = g.box.n[0], n1 = g.box.n[1];
     const int pxy = blockIdx.x * blockDim.x + threadIdx.x;
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
              float4* __restrict__ far4, double* __restrict__ partial, unsigned int* __restrict__ counter,
              double* __restrict__ psi_mean, int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     constexpr int H = P / 2;
     constexpr int LPA = gather_lanes(P);       // lanes per atom
     constexpr int NC = (P + LPA - 1) / LPA;    // stencil columns per lane
@@ -631,6 +634,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __res
                                                       double* __restrict__ energy, int max_atoms,
                                                       int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     __shared__ double red[kWarps][3];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -710,7 +714,8 @@ usr_status grid_kernel_setup(size_t bytes)
 
 #define USR_SPREAD_CASE(PP)                                                                                     \
     case PP:                                                                                                    \
-        k_spread<PP><<<nb, kThreads, smem, st>>>(spos, cell_start, g, tilebuf, partial, counter, mean, status); \
+        launch_pdl(k_spread<PP>, nb, kThreads, smem, st, spos, cell_start, g, tilebuf, partial, counter, mean, \
+                   status);                                                                                     \
         break;
 
 void launch_spread(int P, const float4* spos, const int* cell_start, const GridArgs& g, float* tilebuf, int split,
@@ -729,16 +734,16 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
     }
     const dim3 nr((unsigned)((g.box.n[0] * g.box.n[1] + 255) / 256), (unsigned)g.box.n[2]);
     if (split == 1)
-        k_tile_reduce<1><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32, status);
+        launch_pdl(k_tile_reduce<1>, nr, 256, 0, st, g, tilebuf, mean, rho, rho_lo, rho32, status);
     else if (split == 2)
-        k_tile_reduce<2><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, rho_lo, rho32, status);
+        launch_pdl(k_tile_reduce<2>, nr, 256, 0, st, g, tilebuf, mean, rho, rho_lo, rho32, status);
     else
-        k_tile_reduce<0><<<nr, 256, 0, st>>>(g, tilebuf, mean, rho, nullptr, nullptr, status);
+        launch_pdl(k_tile_reduce<0>, nr, 256, 0, st, g, tilebuf, mean, rho, nullptr, nullptr, status);
 }
 
 #define USR_GATHER_CASE(PP)                                                                \
     case PP:                                                                               \
-        k_gather<PP><<<nb, kGThreads, 0, st>>>(spos, n, psi, g, far4, partial, counter, psi_mean, status); \
+        launch_pdl(k_gather<PP>, nb, kGThreads, 0, st, spos, n, psi, g, far4, partial, counter, psi_mean, status); \
         break;
 
 static int gather_blocks(int n, int P)

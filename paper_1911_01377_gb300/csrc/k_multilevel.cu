@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_ml_restrict(const float* __restrict__ i
                                                      float* __restrict__ out_lo, int d0, int d1, int ncol,
                                                      int n_in, MlTaps taps, long long out_elems, int* status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     __shared__ float S[kMlWinR][kMlPad];
     const int n_out = n_in / 2;
     const int col0 = blockIdx.x * 32, a0 = blockIdx.y * kMlCh, b = blockIdx.z;
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(256) k_ml_prolong(const float* __restrict__ in
                                                     int d1, int ncol, int n_in, MlTaps taps, long long out_elems,
                                                     int* status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     static_assert(kMlWinP <= kMlCh, "the window fits the transpose buffer");
     __shared__ float S[kMlCh][kMlPad];
     const int n_out = 2 * n_in;
@@ -210,7 +212,8 @@ void restrict_axis(const float* in, float* out, float* out_lo, const int* od, co
     int ncol;
     shape<AX>(od, &g, &ncol);
     const long long elems = (long long)od[0] * od[1] * od[2];
-    k_ml_restrict<AX, OUT><<<g, 256, 0, st>>>(in, out, out_lo, od[0], od[1], ncol, 2 * od[AX], w, elems, status);
+    launch_pdl(k_ml_restrict<AX, OUT>, g, 256, 0, st, in, out, out_lo, od[0], od[1], ncol, 2 * od[AX], w, elems,
+               status);
 }
 
 template <int AX, bool ACC>
@@ -220,7 +223,7 @@ void prolong_axis(const float* in, float* out, const int* od, const MlTaps& w, i
     int ncol;
     shape<AX>(od, &g, &ncol);
     const long long elems = (long long)od[0] * od[1] * od[2];
-    k_ml_prolong<AX, ACC><<<g, 256, 0, st>>>(in, out, od[0], od[1], ncol, od[AX] / 2, w, elems, status);
+    launch_pdl(k_ml_prolong<AX, ACC>, g, 256, 0, st, in, out, od[0], od[1], ncol, od[AX] / 2, w, elems, status);
 }
 
 }  // namespace

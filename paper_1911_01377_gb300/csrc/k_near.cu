@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(128, USR_NEAR_MINB) k_near_half(ClusterList L,
                                                                     unsigned long long* __restrict__ acc,
                                                                     double* __restrict__ vir, int* __restrict__ status)
 {
+    pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
     __shared__ float4 sbox[4][GI][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncell = a.box.nc[0] * a.box.nc[1] * a.box.nc[2];
@@ -531,12 +532,12 @@ static void launch_half(int max_groups, const ClusterList& L, const NearArgs& a,
     const int units_max = kNearSplits * max_groups;
     if (vir) {
         static const int2 shape = persistent_shape(k_near_half<GI, DEG, NEXP, true>);
-        k_near_half<GI, DEG, NEXP, true><<<persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st>>>(
-            L, a, queue, acc, vir, status);
+        launch_pdl(k_near_half<GI, DEG, NEXP, true>, persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st, L,
+                   a, queue, acc, vir, status);
     } else {
         static const int2 shape = persistent_shape(k_near_half<GI, DEG, NEXP, false>);
-        k_near_half<GI, DEG, NEXP, false><<<persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st>>>(
-            L, a, queue, acc, nullptr, status);
+        launch_pdl(k_near_half<GI, DEG, NEXP, false>, persistent_grid(shape, ctas_per_sm, units_max), 128, 0, st, L,
+                   a, queue, acc, nullptr, status);
     }
 }
 

@@ -435,6 +435,8 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
 #define ENSURE(ptr, bytes) \
     if ((s = ensure(c, (void**)&(ptr), (bytes))) != USR_OK) return s;
     ENSURE(c->d_count, i4 * c->ncell);
+    // the cell counters start at zero; every evaluation's scan leaves them zero again
+    if (cudaMemsetAsync(c->d_count, 0, i4 * c->ncell, st) != cudaSuccess) return USR_ERR_CUDA;
     ENSURE(c->d_cell_start, i4 * (c->ncell + 1));
     ENSURE(c->d_pstart, i4 * (c->ncell + 1));
     ENSURE(c->d_cpos, f4 * ncl * 8);

@@ -22,6 +22,39 @@ constexpr int kMlT = 16;           // multilevel transfer half-width in fine poi
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
+
+/*
+ * Programmatic dependent launch between consecutive kernels of one stream: a kernel launched with
+ * launch_pdl is scheduled as soon as its predecessor has completed, or earlier, once every CTA of the
+ * predecessor has run pdl_trigger; it calls pdl_wait, which returns when the predecessor has completed
+ * and its writes are visible, before touching anything the predecessor reads or writes.  Only the
+ * cell-list kernels before the fork trigger early: their successors' waiting CTAs then hold SM slots
+ * nothing else needs, whereas waiting CTAs beside the pair kernel and the far chain slowed both.
+ * Without the launch attribute (USR_PDL 0) both calls are no-ops and the launches are ordinary ones.
+ */
+#ifndef USR_PDL
+#define USR_PDL 1
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = USR_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<P>(args)...);
+}
+#endif
 #ifndef USR_GATHER_THREADS
 #define USR_GATHER_THREADS 128
 #endif
