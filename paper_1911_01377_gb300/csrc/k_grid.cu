@@ -180,11 +180,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
     const int Tx = g.tg.T[0], Ty = g.tg.T[1], Tz = g.tg.T[2];
     const int TT = Tx * Ty * Tz;
     const int TXY = Tx * Ty;
+    const int PS = g.tg.ps;                       // plane stride in shared memory (>= TXY, bank-conflict free)
     const BlockGeom bg = block_geom(g, blockIdx.x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         float4* t4 = smem4;
-        for (int t = threadIdx.x; t < (TT >> 2); t += kThreads) t4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = threadIdx.x; t < ((PS * Tz) >> 2); t += kThreads) t4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int natoms = block_rows(g, bg, cell_start, rs, pre);   // contains a barrier
 
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
         // phase 1b: one record per atom, the tile offset of its stencil corner (or -1) and its y
         for (int a = threadIdx.x; a < nch; a += kThreads) {
             const int bx = B[a][0], by = B[a][1], bz = B[a][2];
-            R[a] = make_int2(bx < 0 || by < 0 || bz < 0 ? -1 : (bz * Ty + by) * Tx + bx, by);
+            R[a] = make_int2(bx < 0 || by < 0 || bz < 0 ? -1 : bz * PS + by * Tx + bx, by);
         }
         __syncthreads();
         // phase 2: warp w owns the tile rows ty = w (mod 8); for each atom it adds
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
             static_assert((kWarps & (kWarps - 1)) == 0, "row ownership by a mask");
             const int jx = lane % P, grp = lane / P;
             const int k0 = grp * PG;
-            float* const tl = tile + k0 * TXY + jx;
+            float* const tl = tile + k0 * PS + jx;
             for (int a = 0; a < nch; ++a) {
                 const int2 r = R[a];
                 if (r.x < 0 || grp >= G) continue;
@@ -251,10 +252,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
                     float t[PG];
                     #pragma unroll
                     for (int k = 0; k < PG; ++k)
-                        if (k0 + k < P) t[k] = col[k * TXY];
+                        if (k0 + k < P) t[k] = col[k * PS];
                     #pragma unroll
                     for (int k = 0; k < PG; ++k)
-                        if (k0 + k < P) col[k * TXY] = fmaf(v, wz[k], t[k]);
+                        if (k0 + k < P) col[k * PS] = fmaf(v, wz[k], t[k]);
                 }
             }
         }
@@ -267,8 +268,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread(const float4* __restrict
         const float4* t4 = smem4;
         float4* out4 = reinterpret_cast<float4*>(tilebuf + (size_t)blockIdx.x * TT);
         CSum cs;
+        const int pq = TXY >> 2;                  // float4s per plane (TXY is a multiple of 4)
         for (int t = threadIdx.x; t < (TT >> 2); t += kThreads) {
-            const float4 v = t4[t];
+            const int z = t / pq;
+            const float4 v = t4[z * (PS >> 2) + (t - z * pq)];   // dense in the tile buffer
             out4[t] = v;
             cs.add(v.x);
             cs.add(v.y);
@@ -723,7 +726,7 @@ void launch_spread(int P, const float4* spos, const int* cell_start, const GridA
                    cudaStream_t st, float* rho32)
 {
     const int nb = tile_blocks(g.tg);
-    const size_t smem = sizeof(float) * tile_floats(g.tg);
+    const size_t smem = sizeof(float) * (size_t)g.tg.ps * g.tg.T[2];
     switch (P) {
         USR_SPREAD_CASE(8)
         USR_SPREAD_CASE(10)

@@ -76,6 +76,8 @@ struct TileGeom {
     int nbk[3];     // blocks per axis
     int T[3];       // tile extent per axis (grid points); T[0] % 4 == 0
     int rmax[3];    // reduction-table row length per axis
+    int ps;         // plane stride of the tile in shared memory (floats, >= T[0] T[1], a multiple of 4), chosen
+                    // so that the spread's lanes hit distinct banks
 };
 
 /* Device copies of the per-axis tile tables (owned by the context). */

@@ -413,7 +413,10 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             for (int a = 0; a < 3; ++a) nb *= (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
             return nb;
         };
-        auto bytes = [&]() { return 4.0 * extent(0, tg.kb[0]) * extent(1, tg.kb[1]) * extent(2, tg.kb[2]); };
+        // (the plane stride may grow by up to 28 floats for the bank choice below)
+        auto bytes = [&]() {
+            return 4.0 * (extent(0, tg.kb[0]) * extent(1, tg.kb[1]) + 28) * extent(2, tg.kb[2]);
+        };
         for (int a = 0; a < 3; ++a) tg.kb[a] = std::max(1, std::min(P.cells[a], (int)std::floor(16.0 / wg[a])));
         auto shrink = [&]() {
             int best = -1;
@@ -429,6 +432,26 @@ usr_status make_plan(const usr_params* pp, Plan* out)
         for (int a = 0; a < 3; ++a) {
             tg.nbk[a] = (P.cells[a] + tg.kb[a] - 1) / tg.kb[a];
             tg.T[a] = extent(a, tg.kb[a]);
+        }
+        {
+            // the spread's lane (column jx = lane % P, plane group lane / P of PG planes) touches
+            // (group * PG * ps + jx) mod 32 banks: take the smallest padding with the fewest lanes per bank
+            const int Gp = 32 / P.P, PG = (P.P + Gp - 1) / Gp, txy = tg.T[0] * tg.T[1];
+            int best = 33;
+            for (int pad = 0; pad <= 28; pad += 4) {
+                int hits[32] = {0};
+                int worst = 0;
+                for (int lane = 0; lane < Gp * P.P; ++lane) {
+                    const int b = ((lane / P.P) * PG * (txy + pad) + lane % P.P) % 32;
+                    worst = std::max(worst, ++hits[b]);
+                }
+                if (worst < best) {
+                    best = worst;
+                    tg.ps = txy + pad;
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
             const int H = P.P / 2;
             P.tile_org[a].resize(tg.nbk[a]);
             std::vector<std::vector<int>> lists(P.n[a]);
