@@ -59,7 +59,14 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
     int c = (cz * b.nc[1] + cy) * b.nc[0] + cx;
     if (!USR_IN_BOUNDS(c, b.nc[0] * b.nc[1] * b.nc[2], status)) c = 0;
     cell_of[i] = c;
-    slot[i] = atomicAdd(&count[c], 1);
+    // one atomic per distinct cell in the warp (neighbouring caller indices are often in one cell); the slot
+    // order inside a cell is arbitrary either way, and k_cell_sort orders each cell by caller index
+    const unsigned int peers = __match_any_sync(__activemask(), c);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&count[c], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    slot[i] = base + __popc(peers & ((1u << lane) - 1u));
     wpos[i] = make_float4(xw, yw, zw, (ok && isfinite(p.w)) ? p.w : 0.0f);
 }
 
