@@ -106,8 +106,11 @@ typedef struct {
                                     that wider terms can be handled by multilevel summation): the terms
                                     whose deconvolved width is at least 2.25 coarse spacings on every axis
                                     are convolved on the coarse grid, reached from the fine grid and back
-                                    by Gaussian restriction and prolongation; needs even grid sizes and
-                                    virial = 0.  0: every term on the fine grid */
+                                    by Gaussian restriction and prolongation (33 taps each way); with a
+                                    tensor-core form the coarse passes run in TF32x3 whatever conv says
+                                    (FP32 when a coarse extent is not a multiple of 4). Needs even grid
+                                    sizes of at least 33 points per axis and virial = 0 (USR_ERR_BOX
+                                    otherwise).  0: every term on the fine grid */
 } usr_params;
 
 /* Quantities derived from usr_params (all host-side, FP64). */
