@@ -7,16 +7,28 @@ SRC = os.path.join(HERE, "usr_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
+LIB_SAN = os.path.join(HERE, "liboracle_san.so")
+
+
 def build(force: bool = False) -> str:
-    """Build liboracle.so with gcc (OpenMP, no FP contraction) if it is stale."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           SRC, "-o", tmp, "-lm"]
+    """Build liboracle.so with gcc (OpenMP, no FP contraction) if it is stale.
+
+    With ORACLE_SANITIZE=1 in the environment, build and return liboracle_san.so instead: the same code
+    under AddressSanitizer and UndefinedBehaviorSanitizer (load it with the sanitizer runtimes preloaded,
+    e.g. LD_PRELOAD="$(gcc -print-file-name=libasan.so) $(gcc -print-file-name=libubsan.so)").
+    """
+    san = os.environ.get("ORACLE_SANITIZE") == "1"
+    lib = LIB_SAN if san else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    flags = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+             "-fno-sanitize-recover=undefined"] if san else ["-O2"]
+    cmd = ["gcc"] + flags + ["-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                             SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
