@@ -342,6 +342,18 @@ usr_status usr_cells_static(int n, const float* xyzq, const double* box, const i
  */
 usr_status usr_virial(usr_ctx* ctx, double* W, void* stream);
 
+/*
+ * Net charge Q = sum_i q_i of the last evaluation of a context, summed on the
+ * GPU by the near + far combination (compensated FP32 within a block, FP64
+ * across blocks, fixed order).  A diagnostic: the method assumes a neutral
+ * system (Sec. II), and the k = 0 term that a non-zero Q would carry is the
+ * one Eq. 4 drops, so for Q != 0 the energy is that quadratic form of the
+ * charges.  One double is written to `q` (device or host memory) on `stream`,
+ * ordered after the evaluations enqueued before it; 0 for n = 0 and before
+ * any evaluation.  USR_ERR_ARG for a NULL context or `q`.
+ */
+usr_status usr_net_charge(usr_ctx* ctx, double* q, void* stream);
+
 /* Keep (on != 0) or stop keeping the near and far parts of each usr_eval. */
 usr_status usr_set_keep_parts(usr_ctx* ctx, int on);
 

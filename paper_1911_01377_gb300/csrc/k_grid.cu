@@ -622,9 +622,10 @@ __global__ void __launch_bounds__(kGThreads, (P <= 10 ? USR_GATHER_MINB : 2) * 2
 /*
  * After the pair kernel and the far gather: per sorted atom s, the result in caller order,
  *   out[perm[s]] = (F_near + F_far, phi_near + phi_far - F(0) q),
- * and the energies E = E_near + E_far + E_self (Eq. 20's near sum, the grid part, the self term), the
- * E_near sum per block here, the E_far / E_self sums per tile block from the gather, all reduced in a
- * fixed order by the last block.
+ * and the energies E = E_near + E_far + E_self (1/2 sum q phi over Eq. 20's near part, over the grid part,
+ * and the self term -1/2 F(0) sum q^2), plus the net charge sum q (a diagnostic: the k = 0 term that a
+ * non-zero net charge would carry is the one Eq. 4 drops).  Each block forms the four sums of its atoms;
+ * the last block reduces them in block order.
  */
 __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __restrict__ pos,
                                                       const int* __restrict__ perm,
@@ -634,15 +635,16 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __res
                                                       float4* __restrict__ out, float4* __restrict__ near_dbg,
                                                       float4* __restrict__ far_dbg, double* __restrict__ partial,
                                                       unsigned int* __restrict__ counter,
-                                                      double* __restrict__ energy, int max_atoms,
+                                                      double* __restrict__ energy,
+                                                      double* __restrict__ net_charge, int max_atoms,
                                                       int* __restrict__ status)
 {
     pdl_wait();   // the predecessor on this stream has completed (programmatic launch)
-    __shared__ double red[kWarps][3];
+    __shared__ double red[kWarps][4];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float phi_dc = (float)(*psi_mean) * wsum;   // potential of psi's rounding-level k = 0 mode
-    CSum qn, qf, qq;                                  // sums of q phi_near, q phi_far, q^2
+    CSum qn, qf, qq, qs;                              // sums of q phi_near, q phi_far, q^2, q
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < n; s += gridDim.x * kThreads) {
         const float4 nr = near_part(near_acc, s), f = far4[s];
         const float qi = pos[s].w;
@@ -651,43 +653,45 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const float4* __res
         qn.add_product(qi, nr.w);
         qf.add_product(qi, phi_far);
         qq.add_product(qi, qi);
+        qs.add(qi);
         if (!USR_IN_BOUNDS(i, max_atoms, status)) continue;
         out[i] = make_float4(nr.x + f.x, nr.y + f.y, nr.z + f.z, nr.w + phi_far - F0 * qi);
         if (near_dbg) near_dbg[i] = nr;
         if (far_dbg) far_dbg[i] = make_float4(f.x, f.y, f.z, phi_far);
     }
-    double e[3] = {0.5 * warp_sum_c(qn), 0.5 * warp_sum_c(qf), -0.5 * F0d * warp_sum_c(qq)};
+    double e[4] = {0.5 * warp_sum_c(qn), 0.5 * warp_sum_c(qf), -0.5 * F0d * warp_sum_c(qq), warp_sum_c(qs)};
     if (lane == 0)
-        for (int c = 0; c < 3; ++c) red[warp][c] = e[c];
+        for (int c = 0; c < 4; ++c) red[warp][c] = e[c];
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 4) {
         double v = 0.0;
         for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * 3 + threadIdx.x] = v;
+        partial[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
         __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
-    // the last CTA: the three sums over all CTAs in a fixed order
+    // the last CTA: the four sums over all CTAs in a fixed order
     __threadfence();
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = threadIdx.x; k < (int)gridDim.x; k += kThreads)
-        for (int c = 0; c < 3; ++c) acc[c] += ((volatile double*)partial)[(size_t)k * 3 + c];
-    for (int c = 0; c < 3; ++c) acc[c] = warp_sum_d(acc[c]);
+        for (int c = 0; c < 4; ++c) acc[c] += ((volatile double*)partial)[(size_t)k * 4 + c];
+    for (int c = 0; c < 4; ++c) acc[c] = warp_sum_d(acc[c]);
     __syncthreads();
     if (lane == 0)
-        for (int c = 0; c < 3; ++c) red[warp][c] = acc[c];
+        for (int c = 0; c < 4; ++c) red[warp][c] = acc[c];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v[3] = {0.0, 0.0, 0.0};
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
         for (int w = 0; w < kWarps; ++w)
-            for (int c = 0; c < 3; ++c) v[c] += red[w][c];
+            for (int c = 0; c < 4; ++c) v[c] += red[w][c];
         energy[0] = v[0] + v[1] + v[2];
         energy[1] = v[0];
         energy[2] = v[1];
         energy[3] = v[2];
+        *net_charge = v[3];
         *counter = 0u;
     }
 }
@@ -772,11 +776,12 @@ void launch_gather(int P, int n, const float4* spos, const float* psi, const Gri
 void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
                     const float4* far4, const GridArgs& g, float4* out,
                     float4* near_dbg, float4* far_dbg, double* partial, unsigned int* counter, double* energy,
-                    int* status, cudaStream_t st)
+                    double* net_charge, int* status, cudaStream_t st)
 {
     const int nb = std::max(1, std::min(kCombineBlocks, (n + kThreads - 1) / kThreads));
     k_combine<<<nb, kThreads, 0, st>>>(n, spos, perm, near_acc, far4, g.F0, g.F0d, g.wsum, g.psi_mean, out,
-                                       near_dbg, far_dbg, partial, counter, energy, g.max_atoms, status);
+                                       near_dbg, far_dbg, partial, counter, energy, net_charge, g.max_atoms,
+                                       status);
 }
 
 }  // namespace usr

@@ -78,6 +78,7 @@ struct usr_ctx {
     float *d_rho = nullptr, *d_X = nullptr, *d_Y = nullptr, *d_psi = nullptr;
     float *d_Bx = nullptr, *d_Ay = nullptr, *d_Az = nullptr, *d_wx = nullptr, *d_wy = nullptr, *d_wz = nullptr;
     double *d_spread_partial = nullptr, *d_mean = nullptr, *d_gather_partial = nullptr, *d_energy = nullptr;
+    double* d_netq = nullptr;            // net charge of the last evaluation (FP64)
     unsigned int* d_counters = nullptr;
     double* d_psi_mean = nullptr;
     // spreading tiles and the per-axis tile tables
@@ -151,7 +152,7 @@ void free_all(usr_ctx* c)
                     c->d_pstart, c->d_cidx, c->d_ccell, c->d_cpos, c->d_bblo, c->d_bbhi,
                     c->d_wpos, c->d_spos, c->d_nacc, c->d_gfull, c->d_gpart, c->d_gfirst, c->d_queue, c->d_rho, c->d_X, c->d_Y, c->d_psi, c->d_Bx, c->d_Ay,
                     c->d_Az, c->d_wx, c->d_wy, c->d_wz, c->d_spread_partial, c->d_mean, c->d_gather_partial,
-                    c->d_energy, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_far4, c->d_tilebuf,
+                    c->d_energy, c->d_netq, c->d_counters, c->d_in, c->d_out, c->d_near_dbg, c->d_far_dbg, c->d_far4, c->d_tilebuf,
                     c->d_tab[0], c->d_tab[1], c->d_tab[2], c->d_psi_mean, c->d_ktab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -285,7 +286,7 @@ double usr::plan_device_bytes(const Plan& P)
     b += na * (4 * 4 + 16 * 7 + 32);                                               // per-atom arrays
     const double ngr = near_max_groups((int)na, (int)ncell);
     b += 8 * (ncell + 1) + 4 * ngr + 4;                                            // pair-kernel groups
-    b += 4 * G + 8 * (nsb + kGatherBlocks + 3 * kCombineBlocks) + 8 * 10 + 4 * nsb * tile_floats(P.tile);
+    b += 4 * G + 8 * (nsb + kGatherBlocks + 4 * kCombineBlocks) + 8 * 11 + 4 * nsb * tile_floats(P.tile);
     for (int a = 0; a < 3; ++a) b += 4.0 * ((P.tile_org[a].size() + P.red_cnt[a].size() + 1) / 2 * 2 + P.red_pair[a].size());
     if (P.p.virial) {   // six FP32 table sets, their inputs, two FP32 grids, warp slots, FP32 scratch grids
         b += 6 * 4 * N * (nx * nx + ny * ny + nz * nz + nx + ny + nz) + 6 * 8 * (3 * N * nmax + 4 * N);
@@ -459,9 +460,10 @@ usr_status configure_plan(usr_ctx* c, const Plan& np, cudaStream_t st)
     ENSURE(c->d_psi, fl * G);
     ENSURE(c->d_spread_partial, db * nsb);
     ENSURE(c->d_mean, db);
-    ENSURE(c->d_gather_partial, db * (usr::kGatherBlocks + 3 * usr::kCombineBlocks));
+    ENSURE(c->d_gather_partial, db * (usr::kGatherBlocks + 4 * usr::kCombineBlocks));
     ENSURE(c->d_far4, f4 * na);
     ENSURE(c->d_energy, db * 4);
+    ENSURE(c->d_netq, db);
     ENSURE(c->d_counters, sizeof(unsigned int) * 8);
     ENSURE(c->d_psi_mean, db);
     ENSURE(c->d_in, f4 * na);
@@ -843,7 +845,9 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
     c->prof_valid = false;
     c->vir_valid = false;
     if (n == 0) {
-        if (cudaMemsetAsync(en, 0, 4 * sizeof(double), st) != cudaSuccess) return USR_ERR_CUDA;
+        if (cudaMemsetAsync(en, 0, 4 * sizeof(double), st) != cudaSuccess ||
+            cudaMemsetAsync(c->d_netq, 0, sizeof(double), st) != cudaSuccess)
+            return USR_ERR_CUDA;
         if (c->vir && cudaMemsetAsync(c->d_W, 0, 9 * sizeof(double), st) != cudaSuccess) return USR_ERR_CUDA;
         c->vir_valid = c->vir;
         return USR_OK;
@@ -928,7 +932,8 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
         NvtxRange r("usr: near + far, energy");
         usr::launch_combine(n, c->d_spos, c->d_perm, c->d_nacc, c->d_far4, c->grid, out,
                             c->keep_parts ? c->d_near_dbg : nullptr, c->keep_parts ? c->d_far_dbg : nullptr,
-                            c->d_gather_partial + usr::kGatherBlocks, c->d_counters + 1, en, c->d_status, st);
+                            c->d_gather_partial + usr::kGatherBlocks, c->d_counters + 1, en, c->d_netq,
+                            c->d_status, st);
         mark(10, st);
     }
     if (c->vir) {
@@ -985,7 +990,8 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
     if ((s = configure(c, p, 0)) != USR_OK) return fail(s);
     if (cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess)
+        cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->d_netq, 0, sizeof(double)) != cudaSuccess)
         return fail(USR_ERR_CUDA);
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->ev_made = true;
@@ -1142,6 +1148,16 @@ extern "C" usr_status usr_virial(usr_ctx* c, double* W, void* stream)
 {
     if (!c || !W || !c->vir || !c->vir_valid) return USR_ERR_ARG;
     if (cudaMemcpyAsync(W, c->d_W, 9 * sizeof(double), cudaMemcpyDefault, (cudaStream_t)stream) != cudaSuccess)
+        return USR_ERR_CUDA;
+    return USR_OK;
+}
+
+extern "C" usr_status usr_net_charge(usr_ctx* c, double* q, void* stream)
+{
+    if (!c || !q) return USR_ERR_ARG;
+    usr_status s = check_device(c);
+    if (s != USR_OK) return s;
+    if (cudaMemcpyAsync(q, c->d_netq, sizeof(double), cudaMemcpyDefault, (cudaStream_t)stream) != cudaSuccess)
         return USR_ERR_CUDA;
     return USR_OK;
 }

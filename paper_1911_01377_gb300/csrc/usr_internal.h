@@ -328,10 +328,12 @@ void launch_conv_tc(bool bf16, const ConvTcMaps& m, const ConvTcArgs& g, int bat
 void launch_gather(int P, int n, const float4* spos, const float* psi, const GridArgs& g, float4* far4,
                    double* partial, unsigned int* counter, double* psi_mean, int* status, cudaStream_t st);
 /* near + far in caller order into out (and the parts into near_dbg / far_dbg when non-null); energy[0..3] =
-   total, near, far, self through per-CTA sums in partial (3 per CTA, kCombineBlocks CTAs at most) */
+   total, near, far, self and *net_charge = sum q through per-CTA sums in partial (4 per CTA, kCombineBlocks
+   CTAs at most) */
 void launch_combine(int n, const float4* spos, const int* perm, const unsigned long long* near_acc,
                     const float4* far4, const GridArgs& g, float4* out, float4* near_dbg, float4* far_dbg,
-                    double* partial, unsigned int* counter, double* energy, int* status, cudaStream_t st);
+                    double* partial, unsigned int* counter, double* energy, double* net_charge, int* status,
+                    cudaStream_t st);
 int tile_blocks(const TileGeom& tg);
 size_t tile_floats(const TileGeom& tg);
 usr_status grid_kernel_setup(size_t smem_bytes);

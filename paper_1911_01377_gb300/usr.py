@@ -92,6 +92,7 @@ def lib():
         L.usr_server_destroy.argtypes = [_c_p]
         L.usr_server_destroy.restype = None
         L.usr_virial.argtypes = [_c_p, _c_p, _c_p]
+        L.usr_net_charge.argtypes = [_c_p, _c_p, _c_p]
         L.usr_set_keep_parts.argtypes = [_c_p, _c_i]
         L.usr_debug_parts.argtypes = [_c_p, _c_p, _c_p, _c_p]
         L.usr_set_profiling.argtypes = [_c_p, _c_i]
@@ -101,7 +102,7 @@ def lib():
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
                      "usr_eval_host",
                      "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
-                     "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_server_create", "usr_server_submit",
+                     "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_net_charge", "usr_server_create", "usr_server_submit",
                      "usr_server_wait", "usr_server_info",
                      "usr_debug_parts", "usr_set_profiling", "usr_stage_times", "usr_fp32_peak", "usr_debug_inject_timeout"):
             getattr(L, name).restype = _c_i
@@ -219,6 +220,10 @@ def usr_virial(ctx, W_ptr, stream=None):
     _check(lib().usr_virial(ctx, W_ptr, _stream_ptr(stream)), "usr_virial")
 
 
+def usr_net_charge(ctx, q_ptr, stream=None):
+    _check(lib().usr_net_charge(ctx, q_ptr, _stream_ptr(stream)), "usr_net_charge")
+
+
 def usr_set_keep_parts(ctx, on: bool):
     _check(lib().usr_set_keep_parts(ctx, int(bool(on))), "usr_set_keep_parts")
 
@@ -309,6 +314,14 @@ class USeries:
         W = torch.empty(9, dtype=torch.float64, device="cuda")
         usr_virial(self.ctx, W.data_ptr())
         return W.view(3, 3)
+
+    def net_charge(self, stream=None) -> float:
+        """Net charge sum q of the last evaluation, as summed on the GPU (synchronises the device)."""
+        import torch
+        q = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        usr_net_charge(self.ctx, q.data_ptr(), stream)
+        torch.cuda.synchronize()
+        return float(q[0])
 
     def debug_cells(self, xyzq, stream=None):
         import torch

@@ -1,6 +1,7 @@
 """The C ABI without a GPU: the library builds and loads, exports every entry
 point include/usr.h declares, and its host-side planning agrees with the
 paper and the oracle (no kernel is launched here)."""
+import ctypes
 import math
 import os
 import re
@@ -98,6 +99,15 @@ def test_init_without_gpu_fails_cleanly(libusr):
     with pytest.raises(usr.UsrError) as e:
         usr.usr_init(usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=100))
     assert e.value.code in (4, 5)
+
+
+def test_null_context_arguments_are_refused(libusr):
+    # entry points that read a context refuse a NULL one with USR_ERR_ARG before touching the device
+    q = ctypes.c_double(7.0)
+    assert libusr.usr_net_charge(None, ctypes.addressof(q), None) == 1
+    assert q.value == 7.0
+    assert libusr.usr_virial(None, ctypes.addressof(q), None) == 1
+    assert libusr.usr_last_device_status(None) == 1
 
 
 def test_static_cell_list_refuses_oversized_cell_counts(libusr):

@@ -138,11 +138,14 @@ def test_parts_parity(torch_cuda, name, r_c):
 def test_total_parity(torch_cuda, name, r_c):
     w = workload(name)
     ref = oracle_result(name, r_c)
-    _, g = gpu_eval(torch_cuda, w, r_c)
+    ctx, g = gpu_eval(torch_cuda, w, r_c)
     assert abs(g["E"][0] / ref.E - 1.0) < TOL_E
     assert O.rms_rel(g["out"][:, :3], ref.F) < TOL_F
     assert O.rms_rel(g["out"][:, 3], ref.phi) < TOL_PHI
     assert abs(g["E"][0] - (g["E"][1] + g["E"][2] + g["E"][3])) < 1e-12 * abs(g["E"][0])
+    # neutral inputs (up to the FP32 rounding of the charges): the net charge diagnostic is their exact sum
+    q = w.xyzq[:, 3].astype(np.float64)
+    assert abs(ctx.net_charge() - q.sum()) < 1e-9 * np.abs(q).sum()
 
 
 @pytest.mark.parametrize("r_c", [8.0, 13.0])
@@ -222,10 +225,14 @@ def test_dense_cells_and_non_neutral(torch_cuda):
     xyzq = np.concatenate([pos, q[:, None]], axis=1).astype(np.float32)
     w = W.Workload("dense", box, (32, 32, 32), (9.0,), xyzq)
     ref = O.evaluate(O.Series(*usr_series_tuple("C1_B2")), 9.0, box, xyzq[:, :3], xyzq[:, 3])
-    _, g = gpu_eval(torch, w, 9.0)
+    ctx, g = gpu_eval(torch, w, 9.0)
     assert abs(g["E"][0] / ref.E - 1.0) < 1e-5
     assert O.rms_rel(g["out"][:, :3], ref.F) < TOL_F
     assert O.rms_rel(g["out"][:, 3], ref.phi) < 1e-5
+    # the net charge diagnostic: sum q of the FP32 charges (about 15 e here); one charge more or less
+    # (|q| ~ 0.2) is far outside the tolerance
+    qf = xyzq[:, 3].astype(np.float64)
+    assert abs(ctx.net_charge() - qf.sum()) < 1e-9 * np.abs(qf).sum()
 
 
 @pytest.mark.parametrize("preset", ["C0_B2", "C2_B2"])
@@ -288,6 +295,7 @@ def test_tiny_and_empty(torch_cuda):
     usr.usr_eval(ctx.ctx, 0, x.data_ptr(), out.data_ptr(), en.data_ptr())
     torch.cuda.synchronize()
     assert en.cpu().tolist() == [0.0, 0.0, 0.0, 0.0]
+    assert ctx.net_charge() == 0.0
     # a single charge: self term plus its periodic far images, k = 0 dropped
     one = np.array([[3.0, 4.0, 5.0, 0.7]], dtype=np.float32)
     ref = O.evaluate(O.Series(*usr_series_tuple("C1_B2")), 8.0, box, one[:, :3], one[:, 3])
@@ -295,6 +303,7 @@ def test_tiny_and_empty(torch_cuda):
     torch.cuda.synchronize()
     assert abs(e[0].item() / ref.E - 1.0) < 1e-5
     assert abs(o[0, 3].item() / ref.phi[0] - 1.0) < 1e-5
+    assert ctx.net_charge() == float(np.float32(0.7))
     # capacity is enforced
     big = torch.zeros((5, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(usr.UsrError) as err:
