@@ -24,7 +24,10 @@
  *     makes the copies asynchronous and faster).
  *   - Position/charge and output arrays are float4-packed (x, y, z, q) and
  *     (Fx, Fy, Fz, phi) rows, n rows, 16-byte aligned.
- *   - Positions may lie outside the box; they are wrapped periodically.
+ *   - Positions may lie outside the box; they are wrapped periodically.  The
+ *     single-precision wrap is exact within 2^22 box lengths of the box; a
+ *     row it cannot bring into the box is evaluated as a zero charge at the
+ *     origin and reported as USR_ERR_NONFINITE, like a non-finite row.
  *   - Work is enqueued on the given CUDA stream (cudaStream_t passed as void*,
  *     NULL = legacy default stream) and returns before the GPU finishes,
  *     except where an entry point says it synchronises.  A context must not
@@ -45,7 +48,8 @@ typedef enum {
     USR_OK = 0,
     USR_ERR_ARG = 1,        /* null or misaligned pointer, n < 0, unknown enum value */
     USR_ERR_BOX = 2,        /* geometry the GPU path does not support (see usr_plan) */
-    USR_ERR_NONFINITE = 3,  /* a coordinate was NaN or infinite (found on the GPU) */
+    USR_ERR_NONFINITE = 3,  /* a coordinate or charge was NaN or infinite, or a position lay too far
+                               from the box to be wrapped (found on the GPU) */
     USR_ERR_CUDA = 4,       /* a CUDA runtime call failed */
     USR_ERR_OOM = 5,        /* device memory allocation failed */
     USR_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
@@ -210,7 +214,8 @@ usr_status usr_eval_host_async(usr_ctx* ctx, int n, const float* xyzq, float* ou
 /*
  * Synchronise the context's last stream and return the device status of the
  * evaluations since the previous call, then clear it: USR_OK;
- * USR_ERR_NONFINITE (a non-finite position or charge); USR_ERR_TIMEOUT (a
+ * USR_ERR_NONFINITE (a non-finite position or charge, or a position too far
+ * from the box to be wrapped); USR_ERR_TIMEOUT (a
  * bounded wait of the tensor-core convolution ran out and the pass returned
  * early, its output is not valid); USR_ERR_INTERNAL (a kernel's own
  * consistency check failed).  When several are set, that order decides.
@@ -315,7 +320,8 @@ usr_status usr_debug_pairs(usr_ctx* ctx, int n, const float* xyzq, int* count, u
  * call before any stream capture.  All calls share the array and it keeps the
  * last call's contents; each call clears what must start at zero on its own
  * stream, and calls that overlap on the GPU (unordered streams) race on it.
- * Non-finite rows go to cell 0 as in usr_eval but are not reported.
+ * Non-finite rows, and rows too far from the box to be wrapped, go to cell
+ * 0 at the origin as in usr_eval but are not reported.
  * Cost: each cell is sorted by counting, quadratic in its occupancy, so cell
  * edges should be about the cutoff (tens to hundreds of atoms per cell); a
  * mean occupancy above 2,048 atoms per cell is refused.

@@ -13,7 +13,9 @@
  * Predicate (per axis, RN rounding, no contraction):
  *   k = floorf(x * invL); xw = fmaf(-k, L, x); if (xw < 0) xw += L;
  *   if (xw >= L) xw -= L; cell = min((int)(xw * cs), nc - 1)
- * Non-finite rows go to cell 0 at the origin and raise the status word.
+ * Non-finite rows, and rows so far from the box (beyond about 2^22 box
+ * lengths) that the wrap leaves them outside [0, L], go to cell 0 at the
+ * origin with charge 0 and raise the status word.
  */
 #include "usr_internal.h"
 
@@ -51,6 +53,12 @@ __global__ void __launch_bounds__(256) k_bin_count(int n, const float4* __restri
         xw = canon_wrap(p.x, b.invL[0], b.L[0]);
         yw = canon_wrap(p.y, b.invL[1], b.L[1]);
         zw = canon_wrap(p.z, b.invL[2], b.L[2]);
+        // Within 2^22 box lengths of the box the period count floorf(x / L) is off by at most one and the
+        // wrapped value lies in [0, L] (L itself only by rounding).  Farther out it can be off by more, and
+        // a wrapped value outside the box would send the grid kernels' stencils outside their tiles and
+        // grids: such rows are refused like non-finite ones (a zero charge at the origin, status bit 1).
+        ok = xw >= 0.0f && xw <= b.L[0] && yw >= 0.0f && yw <= b.L[1] && zw >= 0.0f && zw <= b.L[2];
+        if (!ok) xw = yw = zw = 0.0f;
     }
     if (!ok || !isfinite(p.w)) atomicOr(status, 1);
     int cx = canon_cell(xw, b.cs[0], b.nc[0]);

@@ -324,6 +324,35 @@ def test_nonfinite_sets_status(torch_cuda):
     assert usr.usr_last_device_status(ctx.ctx) == 0
 
 
+def test_positions_beyond_the_wrap_are_refused(torch_cuda):
+    """Far outside the box (1e10 A and more here, over 1e8 box lengths) the single-precision wrap's period
+    count floorf(x * (1/L)) is off by several periods, so one correction cannot bring the wrapped value into
+    [0, L].  Such a row is refused like a non-finite one: the status reads USR_ERR_NONFINITE and the row is
+    evaluated as a zero charge at the origin, bit for bit as if it had been given that way; the next
+    evaluation on the context is clean.  One far row per evaluation: refused rows all go to the origin, and
+    two charges at one point (r = 0) are themselves reported as non-finite by the pair kernel."""
+    torch = torch_cuda
+    w = workload("water_3k")
+    ctx = usr.USeries(w.box, w.grid, 9.0, "C1_B2", max_atoms=w.n)
+    for row, ax, x in ((5, 0, 1e10), (6, 1, -1e30), (7, 2, 3.3e13)):
+        far = w.xyzq.copy()
+        far[row, ax] = x
+        L = w.box[ax]
+        k = np.floor(far[row, ax] * np.float32(1.0 / L))     # the wrap's period count, in FP32
+        assert abs(float(k) - float(far[row, ax]) / L) > 3.0
+        origin = w.xyzq.copy()
+        origin[row] = 0.0
+        o_far, e_far = ctx.eval(torch.from_numpy(far).cuda())
+        o_far, e_far = o_far.cpu().numpy(), e_far.cpu().numpy()
+        assert usr.usr_last_device_status(ctx.ctx) == 3
+        assert usr.usr_last_device_status(ctx.ctx) == 0      # cleared
+        o_org, e_org = ctx.eval(torch.from_numpy(origin).cuda())
+        o_org, e_org = o_org.cpu().numpy(), e_org.cpu().numpy()
+        assert usr.usr_last_device_status(ctx.ctx) == 0
+        assert np.array_equal(o_far.view(np.int32), o_org.view(np.int32))
+        assert np.array_equal(e_far.view(np.int64), e_org.view(np.int64))
+
+
 def test_eval_host_matches_device(torch_cuda):
     # the host-buffer entry point runs the same kernels: identical bits
     torch = torch_cuda
