@@ -87,23 +87,26 @@ typedef enum {
  * satisfies Eq. 27 only under that reading.)
  */
 typedef struct {
-    double b;          /* base, b > 1 */
+    double b;          /* base; at least 1.0113, so that the full series down to amplitude
+                          1e-20 of the first term has at most 4096 terms */
     double r0;         /* r_c / sigma */
     double w0;         /* weight of the narrowest Gaussian (1 for C0) */
     double s0;         /* width factor of the narrowest Gaussian (1 for C0, C1) */
-    int n_terms;       /* Gaussians on the far grid; 0 = smallest N whose Eq. 33 bound <= trunc_eps */
+    int n_terms;       /* Gaussians on the far grid (at most 16, and at most the terms of amplitude
+                          >= 1e-20 of the first); 0 = smallest N whose Eq. 33 bound <= trunc_eps */
     double trunc_eps;  /* used when n_terms == 0; 0 means 1e-9 */
 } usr_series;
 
 typedef struct {
     double box[3];               /* box side lengths L_x, L_y, L_z (Angstrom, > 0) */
-    int grid[3];                 /* far-part grid points per axis */
+    int grid[3];                 /* far-part grid points per axis (at most 4096, and at most
+                                    2^31 - 1 in all) */
     double r_c;                  /* near-part cutoff; sigma = r_c / r0 */
     usr_series series;
     double spread_sigma_over_h;  /* spreading Gaussian width / largest grid spacing; 0 = 1.0 */
     int spread_points;           /* spreading stencil points per axis (even, 8..16); 0 = 12 */
     usr_conv conv;
-    int max_atoms;               /* capacity of the context (rows per evaluation) */
+    int max_atoms;               /* capacity of the context (rows per evaluation), at most 2^28 */
     int virial;                  /* 1: also compute the virial tensor (usr_virial); six more far-part
                                     convolution sets per evaluation */
     int multilevel;              /* 1: the wide Gaussian terms on a grid twice as coarse (Sec. V's remark
@@ -145,8 +148,11 @@ usr_status usr_series_preset(int preset, usr_series* out);
  * deconvolved widths sqrt(sigma_j^2 - 2 sigma_s^2) must be real); or one
  * cell's spreading tile would exceed 112 KB of shared memory (cells of more
  * than about 15 grid points per side); or a split convolution form is asked
- * for on a grid whose dimensions are not multiples of 4 (TF32X3) or 8 (BF16X3).
- * USR_ERR_ARG for null pointers or out-of-range series/stencil values.
+ * for on a grid whose dimensions are not multiples of 4 (TF32X3) or 8 (BF16X3);
+ * or a grid beyond 4096 points per axis or 2^31 - 1 points in all.
+ * USR_ERR_ARG for null pointers or out-of-range series/stencil values;
+ * USR_ERR_CAPACITY for max_atoms beyond 2^28; USR_ERR_OOM when the host runs
+ * out of memory (no C++ exception crosses this interface).
  */
 usr_status usr_plan(const usr_params* p, usr_plan_info* out);
 

@@ -958,41 +958,56 @@ usr_status run_eval(usr_ctx* c, int n, const float4* xyzq, float4* out, double* 
 
 }  // namespace
 
+namespace {
+usr_status init_ctx(usr_ctx* c, const usr_params* p);
+}
+
 extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
 {
     if (!out) return USR_ERR_ARG;
     *out = nullptr;
     if (!p) return USR_ERR_ARG;
-    usr_ctx* c = new (std::nothrow) usr_ctx();
-    if (!c) return USR_ERR_OOM;
-    usr_status s = USR_OK;
-    auto fail = [&](usr_status e) {
+    usr_ctx* c = nullptr;
+    try {
+        c = new usr_ctx();
+    } catch (...) {
+        return USR_ERR_OOM;
+    }
+    // on any error, returned or thrown (a failed host allocation), the partly built context is freed here
+    const usr_status s = usr::guard([&] { return init_ctx(c, p); });
+    if (s != USR_OK) {
         free_all(c);
         delete c;
-        return e;
-    };
+        return s;
+    }
+    *out = c;
+    return USR_OK;
+}
+
+namespace {
+
+/* The body of usr_init; the caller frees the context when it returns an error. */
+usr_status init_ctx(usr_ctx* c, const usr_params* p)
+{
+    usr_status s = USR_OK;
     {
         Plan probe;
-        if ((s = usr::make_plan(p, &probe)) != USR_OK) {
-            delete c;
-            return s;
-        }
+        if ((s = usr::make_plan(p, &probe)) != USR_OK) return s;
     }
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
-        delete c;
         return USR_ERR_CUDA;
     }
-    if ((s = usr::grid_kernel_setup(usr::kTileMaxSmem)) != USR_OK) return fail(s);
+    if ((s = usr::grid_kernel_setup(usr::kTileMaxSmem)) != USR_OK) return s;
     if ((s = usr::conv_tc_setup(false, usr::kConvTcMaxSmem)) != USR_OK ||
         (s = usr::conv_tc_setup(true, usr::kConvTcMaxSmem)) != USR_OK)
-        return fail(s);
-    if ((s = configure(c, p, 0)) != USR_OK) return fail(s);
+        return s;
+    if ((s = configure(c, p, 0)) != USR_OK) return s;
     if (cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_energy, 0, 4 * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->d_netq, 0, sizeof(double)) != cudaSuccess)
-        return fail(USR_ERR_CUDA);
+        return USR_ERR_CUDA;
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->ev_made = true;
     {
@@ -1003,12 +1018,13 @@ extern "C" usr_status usr_init(const usr_params* p, usr_ctx** out)
                 != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
-            return fail(USR_ERR_CUDA);
+            return USR_ERR_CUDA;
     }
-    if (cudaDeviceSynchronize() != cudaSuccess) return fail(USR_ERR_CUDA);
-    *out = c;
+    if (cudaDeviceSynchronize() != cudaSuccess) return USR_ERR_CUDA;
     return USR_OK;
 }
+
+}  // namespace
 
 void usr::set_near_ctas_per_sm(usr_ctx* c, int ctas_per_sm)
 {
@@ -1022,7 +1038,7 @@ usr_status usr::reconfigure_with_plan(usr_ctx* c, const Plan& P, cudaStream_t st
     if (s != USR_OK) return s;
     c->parts_valid = false;
     c->prof_valid = false;
-    return configure_plan(c, P, st);
+    return usr::guard([&] { return configure_plan(c, P, st); });
 }
 
 extern "C" usr_status usr_reconfigure(usr_ctx* c, const usr_params* p, void* stream)
@@ -1032,7 +1048,7 @@ extern "C" usr_status usr_reconfigure(usr_ctx* c, const usr_params* p, void* str
     if (s != USR_OK) return s;
     c->parts_valid = false;
     c->prof_valid = false;
-    return configure(c, p, (cudaStream_t)stream);
+    return usr::guard([&] { return configure(c, p, (cudaStream_t)stream); });
 }
 
 extern "C" void usr_destroy(usr_ctx* c)

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include <cuda.h>
@@ -18,8 +19,12 @@ namespace usr {
 constexpr int kMaxPolyDeg = 24;
 constexpr int kMaxExplicit = 8;
 constexpr int kMaxTerms = 16;
+constexpr int kMaxFullTerms = 4096;   // terms of the full real-space series (down to amplitude 1e-20 c)
 constexpr int kMlT = 16;           // multilevel transfer half-width in fine points: ceil(6 x 2.6)
 constexpr int kGridMargin = 8;      // grid points per axis required beyond the stencil width
+constexpr int kMaxGridAxis = 4096;  // grid points per axis at most (bounds the host tables of a plan)
+constexpr long long kMaxGridPoints = (1LL << 31) - 1;   // grid points at most (signed 32-bit headroom)
+constexpr int kMaxAtoms = 1 << 28;  // atoms per context at most (32-bit cluster-slot indices keep headroom)
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
 
@@ -134,6 +139,22 @@ struct Plan {
 
 /* Build the plan (host only).  Returns USR_OK or an error. */
 usr_status make_plan(const usr_params* p, Plan* out);
+
+/*
+ * Run f (returning a usr_status) so that no C++ exception crosses the C ABI: a failed host allocation
+ * becomes USR_ERR_OOM, anything else USR_ERR_INTERNAL.
+ */
+template <typename F>
+usr_status guard(F&& f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return USR_ERR_OOM;
+    } catch (...) {
+        return USR_ERR_INTERNAL;
+    }
+}
 
 /* Device bytes a context holds for a plan (the buffers of usr_api.cu's configure). */
 double plan_device_bytes(const Plan& P);

@@ -98,12 +98,16 @@ usr_status launch(Slot& sl, const Request& r)
     return USR_OK;
 }
 
-/* Plan a request (the slot thread's host work before admission). */
+/* Plan a request (the slot thread's host work before admission): need = -1 for parameters the plan
+   refuses, -2 when the host ran out of memory planning it. */
 void plan_request(Request& r)
 {
     if (r.plan) return;
-    r.plan = std::make_shared<usr::Plan>();
-    r.need = usr::make_plan(&r.params, r.plan.get()) == USR_OK ? usr::plan_device_bytes(*r.plan) : -1.0;
+    const usr_status st = usr::guard([&] {
+        r.plan = std::make_shared<usr::Plan>();
+        return usr::make_plan(&r.params, r.plan.get());
+    });
+    r.need = st == USR_OK ? usr::plan_device_bytes(*r.plan) : (st == USR_ERR_OOM ? -2.0 : -1.0);
 }
 
 double held(const usr_server* s)
@@ -151,7 +155,8 @@ void slot_loop(usr_server* s, int idx)
         plan_request(r);                                     // in parallel with the other slots
         lk.lock();
         // admission by memory: re-targeted to r, the slot holds at most max(its bytes, r's need)
-        usr_status st = r.need < 0.0 ? USR_ERR_BOX : (r.need > budget ? USR_ERR_OOM : USR_OK);
+        usr_status st = r.need == -2.0 ? USR_ERR_OOM
+                        : (r.need < 0.0 ? USR_ERR_BOX : (r.need > budget ? USR_ERR_OOM : USR_OK));
         while (st == USR_OK) {
             const double after = held(s) - sl.bytes + std::max(sl.bytes, r.need);
             if (after <= budget) break;
@@ -208,8 +213,12 @@ extern "C" usr_status usr_server_create(const usr_server_params* p, usr_server**
 {
     if (!out) return USR_ERR_ARG;
     *out = nullptr;
-    usr_server* s = new (std::nothrow) usr_server();
-    if (!s) return USR_ERR_OOM;
+    usr_server* s = nullptr;
+    try {
+        s = new usr_server();
+    } catch (...) {
+        return USR_ERR_OOM;
+    }
     if (p) s->prm = *p;
     else std::memset(&s->prm, 0, sizeof(s->prm));
     if (s->prm.slots <= 0) s->prm.slots = 8;
@@ -223,7 +232,13 @@ extern "C" usr_status usr_server_create(const usr_server_params* p, usr_server**
         delete s;
         return USR_ERR_CUDA;
     }
-    s->slots.resize(s->prm.slots);
+    if (usr::guard([&] {
+            s->slots.resize(s->prm.slots);
+            return USR_OK;
+        }) != USR_OK) {
+        delete s;
+        return USR_ERR_OOM;
+    }
     for (auto& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -232,7 +247,14 @@ extern "C" usr_status usr_server_create(const usr_server_params* p, usr_server**
             return USR_ERR_CUDA;
         }
     }
-    for (int i = 0; i < (int)s->slots.size(); ++i) s->slots[i].th = std::thread(slot_loop, s, i);
+    for (int i = 0; i < (int)s->slots.size(); ++i) {
+        try {
+            s->slots[i].th = std::thread(slot_loop, s, i);
+        } catch (...) {                      // no thread could be started: stop the ones that were
+            usr_server_destroy(s);
+            return USR_ERR_OOM;
+        }
+    }
     *out = s;
     return USR_OK;
 }
@@ -251,9 +273,14 @@ extern "C" usr_status usr_server_submit(usr_server* s, const usr_params* p, int 
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return USR_ERR_ARG;
+        const usr_status st = usr::guard([&] {
+            s->queue.push_back(r);
+            return USR_OK;
+        });
+        if (st != USR_OK) return st;
         r.ticket = s->next_ticket++;
+        s->queue.back().ticket = r.ticket;
         ++s->submitted;
-        s->queue.push_back(r);
     }
     s->cv.notify_all();
     if (ticket) *ticket = r.ticket;

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "usr_internal.h"
@@ -257,8 +258,11 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     const usr_params& p = P.p;
     const usr_series& se = p.series;
     if (!(se.b > 1.0) || !(se.r0 > 0.0) || !(se.w0 > 0.0) || !(se.s0 > 0.0) || se.n_terms < 0 ||
-        se.n_terms > kMaxTerms || se.trunc_eps < 0.0 || !std::isfinite(se.b) || !std::isfinite(se.r0))
+        se.n_terms > kMaxTerms || se.trunc_eps < 0.0 || !std::isfinite(se.b) || !std::isfinite(se.r0) ||
+        !std::isfinite(se.w0) || !std::isfinite(se.s0) || !std::isfinite(se.trunc_eps))
         return USR_ERR_ARG;
+    // the full term table keeps every b^-j >= 1e-20: at most kMaxFullTerms terms (b >= 1.0113)
+    if (std::log(se.b) * (kMaxFullTerms - 1) < std::log(1e20)) return USR_ERR_ARG;
     if (p.conv != USR_CONV_FP32 && p.conv != USR_CONV_TF32X3 && p.conv != USR_CONV_BF16X3) return USR_ERR_ARG;
     if (p.conv != USR_CONV_FP32) {
         const int q = p.conv == USR_CONV_BF16X3 ? 8 : 4;    // 16-byte rows for the tensor maps
@@ -267,20 +271,24 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     }
     if (p.max_atoms < 0 || (p.virial != 0 && p.virial != 1) || (p.multilevel != 0 && p.multilevel != 1))
         return USR_ERR_ARG;
+    if (p.max_atoms > kMaxAtoms) return USR_ERR_CAPACITY;
     int Pst = p.spread_points ? p.spread_points : 12;
     if (Pst < 8 || Pst > 16 || (Pst & 1)) return USR_ERR_ARG;
     double ratio = p.spread_sigma_over_h > 0.0 ? p.spread_sigma_over_h : 1.0;
     if (!(p.r_c > 0.0) || !std::isfinite(p.r_c)) return USR_ERR_BOX;
     for (int a = 0; a < 3; ++a) {
-        if (!(p.box[a] > 0.0) || !std::isfinite(p.box[a]) || p.grid[a] <= 0) return USR_ERR_BOX;
+        if (!(p.box[a] > 0.0) || !std::isfinite(p.box[a]) || p.grid[a] <= 0 || p.grid[a] > kMaxGridAxis)
+            return USR_ERR_BOX;
         P.L[a] = p.box[a];
         P.n[a] = p.grid[a];
         P.h[a] = p.box[a] / p.grid[a];
         if (p.grid[a] < Pst + kGridMargin) return USR_ERR_BOX;
-        int nc = (int)std::floor(p.box[a] / p.r_c);
-        if (nc < 3) return USR_ERR_BOX;
-        P.cells[a] = std::min(nc, 512);
+        // cells of edge >= r_c, at most 512 per axis; clamped in double before the conversion to int
+        const double nc = std::floor(p.box[a] / p.r_c);
+        if (!(nc >= 3.0)) return USR_ERR_BOX;
+        P.cells[a] = (int)std::min(nc, 512.0);
     }
+    if ((long long)p.grid[0] * p.grid[1] * p.grid[2] > kMaxGridPoints) return USR_ERR_BOX;
     P.P = Pst;
     P.sigma = p.r_c / se.r0;
     P.c = 2.0 * std::log(se.b) / std::sqrt(2.0 * kPi * P.sigma * P.sigma);
@@ -305,6 +313,9 @@ usr_status make_plan(const usr_params* pp, Plan* out)
             if (trunc_bound(N, se.b, P.sigma, Lmax) <= eps) { P.N = N; break; }
         if (P.N == 0) return USR_ERR_BOX;
     }
+    // the far terms come from the full table, which stops below amplitude 1e-20 c: a series that asks for
+    // more terms than it holds (a large b with many terms) is refused
+    if (P.N > (int)P.a.size()) return USR_ERR_ARG;
     // spreading Gaussians (width ratio * h per axis, so that every axis has the
     // same stencil reach in widths and the same aliasing) and the per-term,
     // per-axis deconvolved widths sqrt(s_j^2 - 2 sigma_a^2) of Eq. 32.  Per axis,
@@ -527,14 +538,15 @@ extern "C" usr_status usr_series_preset(int preset, usr_series* out)
 extern "C" usr_status usr_plan(const usr_params* p, usr_plan_info* out)
 {
     if (!p || !out) return USR_ERR_ARG;
-    usr::Plan* P = new usr::Plan();
-    usr_status st = usr::make_plan(p, P);
-    if (st == USR_OK) {
-        *out = P->info;
-        out->device_bytes = usr::plan_device_bytes(*P);
-    }
-    delete P;
-    return st;
+    return usr::guard([&] {
+        std::unique_ptr<usr::Plan> P(new usr::Plan());
+        usr_status st = usr::make_plan(p, P.get());
+        if (st == USR_OK) {
+            *out = P->info;
+            out->device_bytes = usr::plan_device_bytes(*P);
+        }
+        return st;
+    });
 }
 
 extern "C" const char* usr_status_string(usr_status s)

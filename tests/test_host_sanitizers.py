@@ -1,8 +1,9 @@
 """Host code under AddressSanitizer and UndefinedBehaviorSanitizer (no GPU).
 
 - The set-up code (`csrc/usr_setup.cpp`: series terms, the pair kernel's fit, periodised kernels, tile tables,
-  the multilevel split) is built with g++ -fsanitize=address,undefined beside a small driver that plans 8,640
-  parameter sets (valid and invalid), and the driver must finish without a report.
+  the multilevel split) is built with g++ -fsanitize=address,undefined,float-cast-overflow beside a small driver
+  that plans 8,640 parameter sets (valid and invalid) and 1,920 sets of extreme and out-of-range values, and the
+  driver must finish without a report.
 - The oracle's C code is rebuilt with the same sanitizers (ORACLE_SANITIZE=1) and its pins run against it in a
   child process with the sanitizer runtimes preloaded.
 Skipped where the compiler has no sanitizer runtimes.
@@ -19,6 +20,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1911_01377_gb300", "csrc")
 CUDA_INC = "/usr/local/cuda/include"
 SAN = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer", "-g", "-O1"]
+# float-to-int conversions out of range are not part of -fsanitize=undefined in GCC: the set-up code gets them too
+SAN_SETUP = SAN + ["-fsanitize=float-cast-overflow", "-fno-sanitize-recover=float-cast-overflow"]
 
 
 def _runtime(name):
@@ -36,7 +39,7 @@ needs_san = pytest.mark.skipif(_runtime("libasan.so") is None or not os.path.isd
 def test_setup_code_under_sanitizers():
     with tempfile.TemporaryDirectory() as d:
         exe = os.path.join(d, "plan_driver")
-        cmd = ["g++", "-std=c++17"] + SAN + ["-I", CUDA_INC, "-I", CSRC,
+        cmd = ["g++", "-std=c++17"] + SAN_SETUP + ["-I", CUDA_INC, "-I", CSRC,
                                              os.path.join(ROOT, "tests", "host_sanitize", "plan_driver.cpp"),
                                              os.path.join(CSRC, "usr_setup.cpp"), "-o", exe]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
