@@ -48,8 +48,9 @@ typedef enum {
     USR_OK = 0,
     USR_ERR_ARG = 1,        /* null or misaligned pointer, n < 0, unknown enum value */
     USR_ERR_BOX = 2,        /* geometry the GPU path does not support (see usr_plan) */
-    USR_ERR_NONFINITE = 3,  /* a coordinate or charge was NaN or infinite, or a position lay too far
-                               from the box to be wrapped (found on the GPU) */
+    USR_ERR_NONFINITE = 3,  /* a coordinate or charge was NaN or infinite, a position lay too far from
+                               the box to be wrapped, or a near-part sum left the fixed-point range
+                               (two charges at one point) (found on the GPU) */
     USR_ERR_CUDA = 4,       /* a CUDA runtime call failed */
     USR_ERR_OOM = 5,        /* device memory allocation failed */
     USR_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
@@ -220,11 +221,13 @@ usr_status usr_eval_host_async(usr_ctx* ctx, int n, const float* xyzq, float* ou
 /*
  * Synchronise the context's last stream and return the device status of the
  * evaluations since the previous call, then clear it: USR_OK;
- * USR_ERR_NONFINITE (a non-finite position or charge, or a position too far
- * from the box to be wrapped); USR_ERR_TIMEOUT (a
- * bounded wait of the tensor-core convolution ran out and the pass returned
- * early, its output is not valid); USR_ERR_INTERNAL (a kernel's own
- * consistency check failed).  When several are set, that order decides.
+ * USR_ERR_NONFINITE (a non-finite position or charge, a position too far
+ * from the box to be wrapped, or a near-part sum beyond the pair kernel's
+ * fixed-point range of +-2^30 per part, as two charges at one point give);
+ * USR_ERR_TIMEOUT (a bounded wait of the tensor-core convolution ran out and
+ * the pass returned early, its output is not valid); USR_ERR_INTERNAL (a
+ * kernel's own consistency check failed).  When several are set, that order
+ * decides.
  */
 usr_status usr_last_device_status(usr_ctx* ctx);
 
