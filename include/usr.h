@@ -99,7 +99,7 @@ typedef struct {
 } usr_series;
 
 typedef struct {
-    double box[3];               /* box side lengths L_x, L_y, L_z (Angstrom, > 0) */
+    double box[3];               /* box side lengths L_x, L_y, L_z (Angstrom, > 0, at most 1e5) */
     int grid[3];                 /* far-part grid points per axis (at most 4096, and at most
                                     2^31 - 1 in all) */
     double r_c;                  /* near-part cutoff; sigma = r_c / r0 */
@@ -150,7 +150,8 @@ usr_status usr_series_preset(int preset, usr_series* out);
  * cell's spreading tile would exceed 112 KB of shared memory (cells of more
  * than about 15 grid points per side); or a split convolution form is asked
  * for on a grid whose dimensions are not multiples of 4 (TF32X3) or 8 (BF16X3);
- * or a grid beyond 4096 points per axis or 2^31 - 1 points in all.
+ * or a grid beyond 4096 points per axis or 2^31 - 1 points in all; or a box
+ * side beyond 1e5 Angstrom.
  * USR_ERR_ARG for null pointers or out-of-range series/stencil values;
  * USR_ERR_CAPACITY for max_atoms beyond 2^28; USR_ERR_OOM when the host runs
  * out of memory (no C++ exception crosses this interface).

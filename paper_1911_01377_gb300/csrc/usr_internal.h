@@ -25,6 +25,8 @@ constexpr int kGridMargin = 8;      // grid points per axis required beyond the 
 constexpr int kMaxGridAxis = 4096;  // grid points per axis at most (bounds the host tables of a plan)
 constexpr long long kMaxGridPoints = (1LL << 31) - 1;   // grid points at most (signed 32-bit headroom)
 constexpr int kMaxAtoms = 1 << 28;  // atoms per context at most (32-bit cluster-slot indices keep headroom)
+constexpr double kMaxBox = 1.0e5;   // box side at most (Angstrom): the pair kernel's padding rows, at -1e6 A and
+                                    // beyond, then stay more than 7e5 A from every atom and periodic image
 constexpr int kGridMeanBlocks = 304;   // CTAs of the grid-mean reduction (two per SM)
 constexpr int kCombineBlocks = 608;    // CTAs of the near + far combination at most (four per SM)
 

@@ -277,7 +277,7 @@ usr_status make_plan(const usr_params* pp, Plan* out)
     double ratio = p.spread_sigma_over_h > 0.0 ? p.spread_sigma_over_h : 1.0;
     if (!(p.r_c > 0.0) || !std::isfinite(p.r_c)) return USR_ERR_BOX;
     for (int a = 0; a < 3; ++a) {
-        if (!(p.box[a] > 0.0) || !std::isfinite(p.box[a]) || p.grid[a] <= 0 || p.grid[a] > kMaxGridAxis)
+        if (!(p.box[a] > 0.0) || !(p.box[a] <= kMaxBox) || p.grid[a] <= 0 || p.grid[a] > kMaxGridAxis)
             return USR_ERR_BOX;
         P.L[a] = p.box[a];
         P.n[a] = p.grid[a];

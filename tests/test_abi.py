@@ -91,17 +91,22 @@ def test_plan_rejects_unsupported_input(libusr):
 
 
 def test_plan_limits(libusr):
-    # the stated limits: at most 4096 grid points per axis and 2^31 - 1 in all (USR_ERR_BOX), 2^28 atoms
+    # the stated limits: at most 4096 grid points per axis and 2^31 - 1 in all and box sides of at most
+    # 1e5 A (USR_ERR_BOX), 2^28 atoms
     # per context (USR_ERR_CAPACITY), a series whose full term table stays within 4096 terms (b >= 1.0113,
     # USR_ERR_ARG); a box-to-cutoff ratio beyond int range is refused, not converted
     ok = dict(box=(31.0, 31.0, 31.0), grid=(32, 32, 32), r_c=9.0, series="C1_B2")
     usr.usr_plan(usr.make_params(**dict(ok, max_atoms=1 << 28)))
     usr.usr_plan(usr.make_params(**dict(ok, series=(1.012, 2.0, 1.0, 1.0), n_terms=3)))
+    usr.usr_plan(usr.make_params(**dict(ok, box=(9.9e4, 300.0, 300.0), grid=(4096, 32, 32), r_c=80.0,
+                                        spread_points=8, spread_sigma_over_h=0.83)))
     cases = [(dict(ok, grid=(4100, 32, 32)), 2),
              (dict(ok, box=(4000.0, 4000.0, 4000.0), grid=(2048, 2048, 1024)), 2),
              (dict(ok, max_atoms=(1 << 28) + 1), 7),
              (dict(ok, series=(1.01, 2.0, 1.0, 1.0), n_terms=3), 1),
-             (dict(ok, box=(1e300, 1e300, 1e300), r_c=1e-300), 2)]
+             (dict(ok, box=(1e300, 1e300, 1e300), r_c=1e-300), 2),
+             (dict(ok, box=(1.2e5, 300.0, 300.0), grid=(4096, 32, 32), r_c=80.0, spread_points=8,
+                   spread_sigma_over_h=0.83), 2)]
     for kw, code in cases:
         with pytest.raises(usr.UsrError) as e:
             usr.usr_plan(usr.make_params(**kw))
