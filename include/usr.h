@@ -196,10 +196,15 @@ usr_status usr_info(const usr_ctx* ctx, usr_plan_info* out);
  *   energy device, 4 doubles: E, E_near, E_far, E_self (may be NULL)
  * n = 0 writes zero energies.  USR_ERR_CAPACITY if n > max_atoms.
  * Internally the far part runs on a second stream of the context, forked from
- * `stream` after the cell list and joined back before the interpolation, so
- * the call stays ordered on `stream` (and capturable) as one unit.  A context's
- * buffers are reused by every call: calls on one context from different
- * streams must be ordered by the caller (an event between them).
+ * `stream` after the cell list and joined back before the near + far
+ * combination, so the call stays ordered on `stream` (and capturable) as one
+ * unit.  A context's buffers are reused by every call: calls on one context
+ * from different streams must be ordered by the caller (an event between
+ * them).  Cost: the cell list orders each cell by counting, quadratic in the
+ * cell's occupancy, and the near part grows with the pairs inside r_c; at the
+ * densities the method is made for (about 0.1 charges per cubic Angstrom)
+ * cells hold tens to a few hundred atoms, while charges piled into one cell
+ * make both stages slow.
  */
 usr_status usr_eval(usr_ctx* ctx, int n, const float* xyzq, float* out, double* energy, void* stream);
 
