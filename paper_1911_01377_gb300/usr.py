@@ -254,6 +254,31 @@ def usr_stage_times(ctx) -> Tuple[float, ...]:
     return tuple(float(v) for v in ms)
 
 
+def _require(t, name: str, cuda: bool, dtype: str, min_numel: int = 0, rows4: bool = False):
+    """Refuse (ValueError) a tensor whose data pointer the library must not be given: not a torch tensor, on
+    the wrong side (device / host), of the wrong dtype, not contiguous, or too small.  rows4: an (n, 4)
+    matrix.  Checked before any library call, so that a wrong buffer never reaches a copy or a kernel."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{name}: a {'CUDA' if cuda else 'host'} tensor is required")
+    if t.dtype != getattr(torch, dtype):
+        raise ValueError(f"{name}: dtype {dtype} is required, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if rows4 and (t.dim() != 2 or t.shape[1] != 4):
+        raise ValueError(f"{name}: shape (n, 4) is required, not {tuple(t.shape)}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: at least {min_numel} elements are required, not {t.numel()}")
+
+
+def _same_device(*ts):
+    devs = {t.device for t in ts}
+    if len(devs) != 1:
+        raise ValueError(f"tensors on different devices: {sorted(str(d) for d in devs)}")
+
+
 class USeries:
     """One evaluation context (a usr_ctx) with torch-tensor conveniences.
 
@@ -266,6 +291,7 @@ class USeries:
         self.ctx = usr_init(self.params)
         self.info = usr_info(self.ctx)
         self.max_atoms = max_atoms
+        self._last_n = None           # rows of the last evaluation made through this object
 
     def reconfigure(self, box, grid, r_c, series="C1_B2", max_atoms=0, stream=None, **kw):
         """Point this context at another system (usr_reconfigure)."""
@@ -273,6 +299,7 @@ class USeries:
         usr_reconfigure(self.ctx, self.params, stream)
         self.info = usr_info(self.ctx)
         self.max_atoms = max_atoms
+        self._last_n = None
 
     def close(self):
         if self.ctx:
@@ -287,25 +314,36 @@ class USeries:
 
     def eval(self, xyzq, out=None, energy=None, stream=None):
         import torch
-        assert xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous() and xyzq.shape[-1] == 4
+        _require(xyzq, "xyzq", cuda=True, dtype="float32", rows4=True)
         n = xyzq.shape[0]
+        if out is not None:
+            _require(out, "out", cuda=True, dtype="float32", min_numel=4 * n)
+        if energy is not None:
+            _require(energy, "energy", cuda=True, dtype="float64", min_numel=4)
         if out is None:
             out = torch.empty((n, 4), dtype=torch.float32, device=xyzq.device)
         if energy is None:
             energy = torch.empty(4, dtype=torch.float64, device=xyzq.device)
+        _same_device(xyzq, out, energy)
         usr_eval(self.ctx, n, xyzq.data_ptr(), out.data_ptr(), energy.data_ptr(), stream)
+        self._last_n = n
         return out, energy
 
     def eval_host(self, xyzq, out=None, energy=None, stream=None):
         """xyzq: (n, 4) float32 host tensor (pinned for asynchronous copies)."""
         import torch
-        assert not xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous()
+        _require(xyzq, "xyzq", cuda=False, dtype="float32", rows4=True)
         n = xyzq.shape[0]
+        if out is not None:
+            _require(out, "out", cuda=False, dtype="float32", min_numel=4 * n)
+        if energy is not None:
+            _require(energy, "energy", cuda=False, dtype="float64", min_numel=4)
         if out is None:
             out = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
         if energy is None:
             energy = torch.empty(4, dtype=torch.float64, pin_memory=True)
         usr_eval_host(self.ctx, n, xyzq.data_ptr(), out.data_ptr(), energy.data_ptr(), stream)
+        self._last_n = n
         return out, energy
 
     def virial(self):
@@ -325,6 +363,7 @@ class USeries:
 
     def debug_cells(self, xyzq, stream=None):
         import torch
+        _require(xyzq, "xyzq", cuda=True, dtype="float32", rows4=True)
         n = xyzq.shape[0]
         ncell = self.info.cells[0] * self.info.cells[1] * self.info.cells[2]
         dev = xyzq.device
@@ -338,6 +377,7 @@ class USeries:
 
     def debug_pairs(self, xyzq):
         import torch
+        _require(xyzq, "xyzq", cuda=True, dtype="float32", rows4=True)
         n = xyzq.shape[0]
         count = torch.empty(n, dtype=torch.int32, device=xyzq.device)
         h = torch.empty(n, dtype=torch.int64, device=xyzq.device)
@@ -345,7 +385,10 @@ class USeries:
         return count, h
 
     def parts(self, n):
+        """Near and far parts of the last evaluation, which had n rows (the library copies that many)."""
         import torch
+        if n != self._last_n:
+            raise ValueError(f"parts({n}): the last evaluation through this object had {self._last_n} rows")
         near = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         far = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         usr_debug_parts(self.ctx, near.data_ptr(), far.data_ptr())
@@ -368,7 +411,11 @@ class Server:
         self._live = {}
 
     def submit(self, params: usr_params, xyzq, out, energy=None) -> int:
+        _require(xyzq, "xyzq", cuda=False, dtype="float32", rows4=True)
         n = int(xyzq.shape[0])
+        _require(out, "out", cuda=False, dtype="float32", min_numel=4 * n)
+        if energy is not None:
+            _require(energy, "energy", cuda=False, dtype="float64", min_numel=4)
         t = ctypes.c_longlong(0)
         _check(lib().usr_server_submit(self.handle, ctypes.byref(params), n, xyzq.data_ptr(), out.data_ptr(),
                                        energy.data_ptr() if energy is not None else None, ctypes.byref(t)),

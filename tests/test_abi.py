@@ -133,6 +133,42 @@ def test_null_context_arguments_are_refused(libusr):
     assert libusr.usr_last_device_status(None) == 1
 
 
+def test_binding_refuses_unusable_tensors():
+    # the binding checks every tensor whose pointer it hands to the library before any library call: wrong
+    # side (host / device), dtype, layout or size raise ValueError (runs without a GPU: every case fails
+    # before a context is touched)
+    import torch
+    ctx = usr.USeries.__new__(usr.USeries)
+    ctx.ctx, ctx._last_n = 0, None
+    x = torch.zeros((10, 4), dtype=torch.float32)
+    bad_device = [x, torch.zeros((10, 4), dtype=torch.float64), x.t(), torch.zeros(40, dtype=torch.float32)]
+    for t in bad_device:
+        with pytest.raises(ValueError):
+            ctx.eval(t)
+        with pytest.raises(ValueError):
+            ctx.debug_cells(t)
+        with pytest.raises(ValueError):
+            ctx.debug_pairs(t)
+    for t in [x.double(), x.t(), x.reshape(40), x[:, :3].contiguous(), "not a tensor"]:
+        with pytest.raises(ValueError):
+            ctx.eval_host(t)
+    with pytest.raises(ValueError):                                   # out too small
+        ctx.eval_host(x, out=torch.zeros((9, 4), dtype=torch.float32))
+    with pytest.raises(ValueError):                                   # energy too small / wrong dtype
+        ctx.eval_host(x, out=torch.zeros((10, 4), dtype=torch.float32), energy=torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        ctx.eval_host(x, out=torch.zeros((10, 4), dtype=torch.float32), energy=torch.zeros(4, dtype=torch.float32))
+    with pytest.raises(ValueError):                                   # parts() only after an evaluation of n rows
+        ctx.parts(10)
+    srv = usr.Server.__new__(usr.Server)
+    srv.handle, srv._live = 0, {}
+    p = usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=10)
+    for args in [(x.double(), torch.zeros((10, 4))), (x, torch.zeros((10, 3))), (x, torch.zeros((10, 4)).double()),
+                 (x, torch.zeros((10, 4)), torch.zeros(2, dtype=torch.float64))]:
+        with pytest.raises(ValueError):
+            srv.submit(p, *args)
+
+
 def test_static_cell_list_refuses_oversized_cell_counts(libusr):
     """usr_cells_static checks every cell factor before multiplying, so a product that would overflow
     64 bits is refused as a capacity error before any device call (null buffers: nothing is touched)."""
