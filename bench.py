@@ -50,8 +50,9 @@ SWEEP = (8.0, 9.0, 10.0, 11.0, 12.0, 13.0)
 # conv z, grid_mean, gather
 KERNELS_PER_EVAL = 12
 FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock
-# algorithmic flops of one unordered pair inside r_c (the survey's 30-50 flop estimate of the pair
-# arithmetic, its midpoint), the unit of the pair kernel's roofline
+# algorithmic flops of one unordered pair inside r_c, the unit of the pair kernel's roofline: the midpoint of
+# 30-50 flops for the arithmetic any pair kernel of Eq. 20 needs (the displacement and r^2, 1/r, F(r) and its
+# derivative, the force on both atoms and both potentials), independent of how this kernel evaluates F
 NEAR_FLOPS_PER_PAIR = 40
 # DRAM bytes (read + write) per launch of the pair kernel over this sweep, averaged over its six launches (one
 # per cutoff) in one ncu capture of `bench.py --steps 1 --warmup 3 --serve-systems 0 --no-scale`; None whenever
@@ -492,9 +493,10 @@ def run_gpu(args):
                             if peak_ok else "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"),
             "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
             "flops_per_pair": NEAR_FLOPS_PER_PAIR,
-            "flops_per_pair_note": "algorithmic: the survey's 30-50 flops per pair inside r_c, midpoint; the kernel's "
-                                   "own arithmetic is " + ", ".join(str(near_flops_per_pair(i.poly_degree, i.n_explicit))
-                                                                    for i in infos[:1]) + " per pair",
+            "flops_per_pair_note": "algorithmic: 30-50 flops per pair inside r_c (Eq. 20's pair arithmetic), "
+                                   "midpoint; the kernel's own arithmetic is "
+                                   + ", ".join(str(near_flops_per_pair(i.poly_degree, i.n_explicit)) for i in infos[:1])
+                                   + " per pair",
             "pairs_per_eval": pairs, "launch_ms_mean": 1e3 * t_dom / len(SWEEP)}
 
     # stage-wise floors of the chosen form, summed over the sweep, against the measured stage times

@@ -100,11 +100,10 @@ def lib():
         L.usr_fp32_peak.argtypes = [ctypes.POINTER(_c_d)]
         L.usr_debug_inject_timeout.argtypes = [_c_p, _c_i]
         for name in ("usr_series_preset", "usr_plan", "usr_init", "usr_reconfigure", "usr_info", "usr_eval",
-                     "usr_eval_host",
-                     "usr_last_device_status", "usr_debug_cells", "usr_debug_pairs", "usr_cells_static",
-                     "usr_set_keep_parts", "usr_eval_host_async", "usr_virial", "usr_net_charge", "usr_server_create", "usr_server_submit",
-                     "usr_server_wait", "usr_server_info",
-                     "usr_debug_parts", "usr_set_profiling", "usr_stage_times", "usr_fp32_peak", "usr_debug_inject_timeout"):
+                     "usr_eval_host", "usr_eval_host_async", "usr_last_device_status", "usr_debug_cells",
+                     "usr_debug_pairs", "usr_cells_static", "usr_set_keep_parts", "usr_virial", "usr_net_charge",
+                     "usr_server_create", "usr_server_submit", "usr_server_wait", "usr_server_info", "usr_debug_parts",
+                     "usr_set_profiling", "usr_stage_times", "usr_fp32_peak", "usr_debug_inject_timeout"):
             getattr(L, name).restype = _c_i
         _lib = L
     return _lib
