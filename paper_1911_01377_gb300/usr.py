@@ -223,6 +223,49 @@ def usr_net_charge(ctx, q_ptr, stream=None):
     _check(lib().usr_net_charge(ctx, q_ptr, _stream_ptr(stream)), "usr_net_charge")
 
 
+def usr_server_create(hbm_budget_bytes=0.0, slots=0) -> int:
+    p = usr_server_params(float(hbm_budget_bytes), int(slots))
+    h = _c_p()
+    _check(lib().usr_server_create(ctypes.byref(p), ctypes.byref(h)), "usr_server_create")
+    return h.value
+
+
+def usr_server_submit(server, params: usr_params, n: int, xyzq_ptr: int, out_ptr: int,
+                      energy_ptr: Optional[int]) -> int:
+    t = ctypes.c_longlong(0)
+    _check(lib().usr_server_submit(server, ctypes.byref(params), int(n), xyzq_ptr, out_ptr, energy_ptr,
+                                   ctypes.byref(t)), "usr_server_submit")
+    return t.value
+
+
+def usr_server_poll(server, max_n: int = 1024):
+    """Completed requests as (ticket, latency_ms, status) tuples (at most max_n)."""
+    if max_n <= 0:
+        return []
+    tk = (ctypes.c_longlong * max_n)()
+    lat = (_c_d * max_n)()
+    st = (_c_i * max_n)()
+    k = lib().usr_server_poll(server, tk, lat, st, int(max_n))
+    return [(int(tk[i]), float(lat[i]), int(st[i])) for i in range(k)]
+
+
+def usr_server_wait(server, timeout_s: float = 0.0):
+    _check(lib().usr_server_wait(server, float(timeout_s)), "usr_server_wait")
+
+
+def usr_server_info(server) -> Tuple[float, int, int]:
+    """(device bytes the slots hold, requests waiting for admission, requests on the device)."""
+    b = _c_d(0.0)
+    q = ctypes.c_longlong(0)
+    f = ctypes.c_longlong(0)
+    _check(lib().usr_server_info(server, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)), "usr_server_info")
+    return float(b.value), int(q.value), int(f.value)
+
+
+def usr_server_destroy(server):
+    lib().usr_server_destroy(server)
+
+
 def usr_set_keep_parts(ctx, on: bool):
     _check(lib().usr_set_keep_parts(ctx, int(bool(on))), "usr_set_keep_parts")
 
@@ -403,10 +446,7 @@ class Server:
     """
 
     def __init__(self, hbm_budget_bytes=0.0, slots=0):
-        p = usr_server_params(float(hbm_budget_bytes), int(slots))
-        h = _c_p()
-        _check(lib().usr_server_create(ctypes.byref(p), ctypes.byref(h)), "usr_server_create")
-        self.handle = h.value
+        self.handle = usr_server_create(hbm_budget_bytes, slots)
         self._live = {}
 
     def submit(self, params: usr_params, xyzq, out, energy=None) -> int:
@@ -415,38 +455,26 @@ class Server:
         _require(out, "out", cuda=False, dtype="float32", min_numel=4 * n)
         if energy is not None:
             _require(energy, "energy", cuda=False, dtype="float64", min_numel=4)
-        t = ctypes.c_longlong(0)
-        _check(lib().usr_server_submit(self.handle, ctypes.byref(params), n, xyzq.data_ptr(), out.data_ptr(),
-                                       energy.data_ptr() if energy is not None else None, ctypes.byref(t)),
-               "usr_server_submit")
-        self._live[t.value] = (params, xyzq, out, energy)
-        return t.value
+        t = usr_server_submit(self.handle, params, n, xyzq.data_ptr(), out.data_ptr(),
+                              energy.data_ptr() if energy is not None else None)
+        self._live[t] = (params, xyzq, out, energy)
+        return t
 
     def poll(self, max_n=1024):
-        tk = (ctypes.c_longlong * max_n)()
-        lat = (_c_d * max_n)()
-        st = (_c_i * max_n)()
-        k = lib().usr_server_poll(self.handle, tk, lat, st, max_n)
-        res = []
-        for i in range(k):
-            self._live.pop(tk[i], None)
-            res.append((int(tk[i]), float(lat[i]), int(st[i])))
+        res = usr_server_poll(self.handle, max_n)
+        for tk, _, _ in res:
+            self._live.pop(tk, None)
         return res
 
     def wait(self, timeout_s=0.0):
-        _check(lib().usr_server_wait(self.handle, float(timeout_s)), "usr_server_wait")
+        usr_server_wait(self.handle, timeout_s)
 
     def info(self):
-        b = _c_d(0.0)
-        q = ctypes.c_longlong(0)
-        f = ctypes.c_longlong(0)
-        _check(lib().usr_server_info(self.handle, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)),
-               "usr_server_info")
-        return float(b.value), int(q.value), int(f.value)
+        return usr_server_info(self.handle)
 
     def close(self):
         if self.handle:
-            lib().usr_server_destroy(self.handle)
+            usr_server_destroy(self.handle)
             self.handle = 0
             self._live.clear()
 

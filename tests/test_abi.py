@@ -133,6 +133,36 @@ def test_null_context_arguments_are_refused(libusr):
     assert libusr.usr_last_device_status(None) == 1
 
 
+def test_binding_has_every_entry_point(libusr):
+    # the Python binding carries every entry point of the C ABI under the same name
+    missing = [name for name in _declared() if not callable(getattr(usr, name, None))]
+    assert not missing, missing
+
+
+def test_server_entry_points_without_a_server(libusr):
+    # the serving entry points check their arguments before touching the device: a NULL server is refused,
+    # and so are parameters out of range (these run without a GPU)
+    import torch
+    for kw in (dict(slots=65), dict(hbm_budget_bytes=-1.0)):
+        with pytest.raises(usr.UsrError) as e:
+            usr.usr_server_create(**kw)
+        assert e.value.code == 1
+    assert usr.usr_server_poll(0) == [] and usr.usr_server_poll(0, 0) == []
+    for call in (lambda: usr.usr_server_wait(0, 0.1), lambda: usr.usr_server_info(0)):
+        with pytest.raises(usr.UsrError) as e:
+            call()
+        assert e.value.code == 1
+    usr.usr_server_destroy(0)                                  # NULL is ignored
+    srv = usr.Server.__new__(usr.Server)
+    srv.handle, srv._live = 0, {}
+    p = usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=10)
+    x, o, e4 = torch.zeros((10, 4)), torch.zeros((10, 4)), torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(usr.UsrError) as e:
+        srv.submit(p, x, o, e4)
+    assert e.value.code == 1 and srv._live == {}
+    assert srv.poll() == []
+
+
 def test_binding_refuses_unusable_tensors():
     # the binding checks every tensor whose pointer it hands to the library before any library call: wrong
     # side (host / device), dtype, layout or size raise ValueError (runs without a GPU: every case fails
