@@ -163,6 +163,59 @@ def test_server_entry_points_without_a_server(libusr):
     assert srv.poll() == []
 
 
+class _FakeServerLib:
+    """Stands in for libusr's serving entry points: records submissions and completes them in order."""
+
+    def __init__(self):
+        self.pending, self.next = [], 0
+
+    def usr_server_create(self, p, h):
+        assert p._obj.slots == 3 and p._obj.hbm_budget_bytes == 1e9
+        h._obj.value = 1234
+        return 0
+
+    def usr_server_submit(self, s, p, n, x, o, e, t):
+        assert s == 1234 and n == 10 and x and o and e and p._obj.max_atoms == 10
+        t._obj.value = self.next
+        self.pending.append(self.next)
+        self.next += 1
+        return 0
+
+    def usr_server_poll(self, s, tk, lat, st, m):
+        k = min(m, len(self.pending))
+        for i in range(k):
+            tk[i], lat[i], st[i] = self.pending[i], 0.5 + i, 0
+        self.pending = self.pending[k:]
+        return k
+
+    def usr_server_wait(self, s, t):
+        return 0 if s == 1234 else 1
+
+    def usr_server_info(self, s, b, q, f):
+        b._obj.value, q._obj.value, f._obj.value = 7.0, 1, 2
+        return 0
+
+    def usr_server_destroy(self, s):
+        assert s == 1234
+
+
+def test_server_wrapper_bookkeeping(libusr, monkeypatch):
+    # the Server class marshals through the usr_server_* wrappers and keeps each request's tensors referenced
+    # until poll() returns its ticket (the library itself replaced by a fake: no GPU)
+    import torch
+    p = usr.make_params((31.0,) * 3, (32,) * 3, 9.0, "C1_B2", max_atoms=10)
+    monkeypatch.setattr(usr, "_lib", _FakeServerLib())
+    srv = usr.Server(hbm_budget_bytes=1e9, slots=3)
+    x, o, e = torch.zeros((10, 4)), torch.zeros((10, 4)), torch.zeros(4, dtype=torch.float64)
+    assert (srv.submit(p, x, o, e), srv.submit(p, x, o, e)) == (0, 1) and set(srv._live) == {0, 1}
+    srv.wait(5)
+    assert srv.info() == (7.0, 1, 2)
+    assert srv.poll(1) == [(0, 0.5, 0)] and set(srv._live) == {1}
+    assert srv.poll() == [(1, 0.5, 0)] and srv._live == {}
+    srv.close()
+    assert srv.handle == 0
+
+
 def test_binding_refuses_unusable_tensors():
     # the binding checks every tensor whose pointer it hands to the library before any library call: wrong
     # side (host / device), dtype, layout or size raise ValueError (runs without a GPU: every case fails
