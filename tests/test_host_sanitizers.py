@@ -3,7 +3,9 @@
 - The set-up code (`csrc/usr_setup.cpp`: series terms, the pair kernel's fit, periodised kernels, tile tables,
   the multilevel split) is built with g++ -fsanitize=address,undefined,float-cast-overflow beside a small driver
   that plans 8,640 parameter sets (valid and invalid) and 1,920 sets of extreme and out-of-range values, and the
-  driver must finish without a report.
+  driver must finish without a report.  For every valid plan of the first sweep the driver also checks, exactly in
+  single precision, that the spreading stencil of every wrapped coordinate fits the shared-memory tile of its
+  block of cells (the spreading kernel's tile-base check then never fires).
 - The oracle's C code is rebuilt with the same sanitizers (ORACLE_SANITIZE=1) and its pins run against it in a
   child process with the sanitizer runtimes preloaded.
 Skipped where the compiler has no sanitizer runtimes.
@@ -39,14 +41,14 @@ needs_san = pytest.mark.skipif(_runtime("libasan.so") is None or not os.path.isd
 def test_setup_code_under_sanitizers():
     with tempfile.TemporaryDirectory() as d:
         exe = os.path.join(d, "plan_driver")
-        cmd = ["g++", "-std=c++17"] + SAN_SETUP + ["-I", CUDA_INC, "-I", CSRC,
+        cmd = ["g++", "-std=c++17", "-ffp-contract=off"] + SAN_SETUP + ["-I", CUDA_INC, "-I", CSRC,
                                              os.path.join(ROOT, "tests", "host_sanitize", "plan_driver.cpp"),
                                              os.path.join(CSRC, "usr_setup.cpp"), "-o", exe]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
         r = subprocess.run([exe], capture_output=True, text=True, timeout=600,
                            env=dict(os.environ, ASAN_OPTIONS="detect_leaks=1:abort_on_error=1"))
         assert r.returncode == 0, r.stderr[-4000:]
-        assert "plans ok" in r.stdout and "runtime error" not in r.stderr
+        assert "plans ok" in r.stdout and "tile violations 0" in r.stdout and "runtime error" not in r.stderr
 
 
 @needs_san
