@@ -45,6 +45,16 @@ int check_spread_tiles(const usr::Plan& P)
 {
     int bad = 0;
     const int H = P.P / 2;
+    // the tile's own layout: x extent a multiple of 4 (float4 zeroing), a plane stride of at least one plane
+    // and a multiple of 4, at most kTileMaxSmem bytes, and at most 64 (z, y) rows of cells per block (the
+    // spreading kernel's row table)
+    const usr::TileGeom& tg = P.tile;
+    if (tg.T[0] % 4 != 0 || tg.ps < tg.T[0] * tg.T[1] || tg.ps % 4 != 0 ||
+        4.0 * tg.ps * tg.T[2] > usr::kTileMaxSmem || tg.kb[1] * tg.kb[2] > 64) {
+        if (bad < 5) std::printf("tile layout violation: T %d %d %d ps %d kb %d %d %d\n", tg.T[0], tg.T[1], tg.T[2],
+                                 tg.ps, tg.kb[0], tg.kb[1], tg.kb[2]);
+        ++bad;
+    }
     for (int a = 0; a < 3; ++a) {
         const float L = (float)P.L[a], cs = (float)((double)P.cells[a] / P.L[a]);
         const float gs = (float)((double)P.n[a] / P.L[a]);
