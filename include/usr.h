@@ -151,7 +151,10 @@ usr_status usr_series_preset(int preset, usr_series* out);
  * than about 15 grid points per side); or a split convolution form is asked
  * for on a grid whose dimensions are not multiples of 4 (TF32X3) or 8 (BF16X3);
  * or a grid beyond 4096 points per axis or 2^31 - 1 points in all; or a box
- * side beyond 1e5 Angstrom.
+ * side beyond 1e5 Angstrom; or, with n_terms = 0, a bound of Eq. 33 that
+ * needs more than 16 far terms (the small-b rows of Table 1 on boxes of
+ * about 80 Angstrom and more: set n_terms, at most 16, to accept a larger
+ * truncation error).
  * USR_ERR_ARG for null pointers or out-of-range series/stencil values;
  * USR_ERR_CAPACITY for max_atoms beyond 2^28; USR_ERR_OOM when the host runs
  * out of memory (no C++ exception crosses this interface).
