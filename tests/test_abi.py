@@ -282,3 +282,14 @@ def test_multilevel_plan(libusr):
     with pytest.raises(usr.UsrError) as e:
         usr.usr_plan(usr.make_params(box, grid, 10.0, "C1_B2", max_atoms=10, multilevel=2))
     assert e.value.code == 1
+
+
+def test_autograd_refuses_unusable_inputs():
+    # the differentiable energy checks its inputs before any evaluation (runs without a GPU)
+    import torch
+    from paper_1911_01377_gb300.autograd import usr_energy
+    xyz, q = torch.zeros((5, 3)), torch.zeros(5)
+    with pytest.raises(TypeError):
+        usr_energy(xyz, q, None)                                  # host tensors
+    with pytest.raises(TypeError):
+        usr_energy(xyz.double(), q.double(), None)
