@@ -19,11 +19,13 @@ def build(force: bool = False) -> str:
     """
     san = os.environ.get("ORACLE_SANITIZE") == "1"
     lib = LIB_SAN if san else LIB
-    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+    # stale when the source or this file (its flags) is newer than the library
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(os.path.abspath(__file__)))
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
         return lib
     tmp = lib + ".tmp%d" % os.getpid()
-    flags = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
-             "-fno-sanitize-recover=undefined"] if san else ["-O2"]
+    flags = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined,float-cast-overflow",
+             "-fno-sanitize-recover=undefined,float-cast-overflow"] if san else ["-O2"]
     cmd = ["gcc"] + flags + ["-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
                              SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)

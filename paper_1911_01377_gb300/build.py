@@ -35,7 +35,9 @@ def _stale(lib: str) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(HERE, "..", "include", "usr.h")]
+    # the sources, the headers, and this file (the compiler flags)
+    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(HERE, "..", "include", "usr.h"),
+                                                              os.path.abspath(__file__)]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
